@@ -1,0 +1,357 @@
+"""Benchmark of the tiled sparse LBM step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A benchmark step is one LBM time step (stage neighbourhood, gather, collide,
+store, swap) over the whole synthetic geometry; every 100 steps the FP64
+mass / momentum / residual reduction runs as well.  The default workload is
+the D3Q19 FP64 sphere pack: 256^3 lattice, 4^3 tiles, 30% fluid, tau 0.6,
+force 1e-6 along periodic x.  The metric is MLUPS over fluid nodes (Eq. 43 of
+the paper counts only non-solid nodes) and the fraction of the HBM roofline
+(B_node = 304 B per update, Eq. 10).
+
+With N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(the step does not shard on one box: replicas only) and the value is the sum
+over ranks.  ``--impl reference`` times the FP64 CPU oracle instead, on the
+host cores, on a 64^3 crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1703_08015_gb300 import geometry as geo  # noqa: E402
+from paper_1703_08015_gb300 import perfmodel as pm  # noqa: E402
+
+STATS_EVERY = 100
+B_NODE = {9: pm.B_node(9, 8), 19: pm.B_node(19, 8)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="d3q19_spheres_256")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--arith", default="auto", choices=["auto", "f64", "fixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a window."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = list(csv.reader(io.StringIO(out)))
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 10:
+                continue
+            try:
+                sm.append(float(r[2]))
+                smax = float(r[3])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if r[6 + k].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1703_08015_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload, arith):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(f"{workload}:{arith}")
+    if not e or e.get("kernel_source_sha") != kernel_source_sha():
+        return None, None
+    return e.get("dram_bytes_per_launch"), e.get("note")
+
+
+def cpu_baseline(mask, params, seconds=10.0, min_steps=2):
+    """The FP64 oracle, as it stands, on a 64^3 crop of the workload."""
+    import oracle
+
+    crop = np.ascontiguousarray(mask[:64, :64, :64]) if mask.shape[0] > 1 else np.ascontiguousarray(mask)
+    lat = params["lattice"]
+    per = params["periodic"]
+    f = oracle.init(lat, crop)
+    g = np.empty_like(f)
+    oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)  # warm-up
+    n = 0
+    t0 = time.perf_counter()
+    while n < min_steps or time.perf_counter() - t0 < seconds:
+        oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)
+        f, g = g, f
+        n += 1
+    dt = time.perf_counter() - t0
+    nf = int(crop.sum())
+    return {"value": nf * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(0), "kind": "oracle",
+            "sample": f"{n} oracle steps on the {crop.shape[2]}x{crop.shape[1]}x{crop.shape[0]} corner "
+                      f"crop ({nf} fluid nodes) of the workload, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    mask, params, info = geo.workload(args.workload)
+    crop = np.ascontiguousarray(mask[:64, :64, :64]) if mask.shape[0] > 1 else np.ascontiguousarray(mask)
+    lat = params["lattice"]
+    per = params["periodic"]
+    f = oracle.init(lat, crop)
+    g = np.empty_like(f)
+    for _ in range(args.warmup):
+        oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)
+        f, g = g, f
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)
+        f, g = g, f
+    dt = time.perf_counter() - t0
+    nf = int(crop.sum())
+    v = nf * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": "D3Q19 sparse MLUPS" if lat == 19 else "D2Q9 sparse MLUPS",
+            "value": v, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "crop": list(crop.shape[::-1]), "fluid_nodes": nf},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(0), "kind": "oracle",
+                             "sample": f"each step: one oracle step on the 64^3 corner crop ({nf} fluid nodes)"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1703_08015_gb300 import lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mask, params, info = geo.workload(args.workload)
+    lat, a = params["lattice"], params["tile_a"]
+    arith = {"auto": lbm.LBM_ARITH_AUTO, "f64": lbm.LBM_ARITH_F64, "fixed": lbm.LBM_ARITH_FIXED}[args.arith]
+    solver = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], arith=arith,
+                        device=dev)
+    stream = solver.stream
+    n_fluid = int(solver.tiling.n_fluid)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(3, args.warmup) // 20 + 1):
+        solver.step(20)
+    solver.stats(residual=True)
+    barrier()
+
+    sampler = ClockSampler(local)
+    ev = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    t_start.record(stream)
+    left = args.steps
+    while left > 0:
+        k = min(STATS_EVERY, left)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(k)
+        e1.record(stream)
+        ev.append((e0, e1, k))
+        launches += k
+        left -= k
+        if k == STATS_EVERY:
+            st = lbm.lbm_stats()
+            lbm.lbm_moments(solver.ctx, None, None, st, lbm.LBM_STATS_RESIDUAL, solver._s())
+            launches += 2
+    t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end)
+    step_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
+    ms_all = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_all.item())
+    value = n_fluid * args.steps * world / (ms_max * 1e-3) / 1e6
+    arith_name = {lbm.LBM_ARITH_AUTO: "fixed", lbm.LBM_ARITH_FIXED: "fixed", lbm.LBM_ARITH_F64: "f64"}[arith]
+    tiling = solver.tiling
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(mask, params, args.steps, arith, dev, world)
+
+    if rank != 0:
+        return
+    peaks, peak_kind = load_peaks()
+    bytes_per_launch = n_fluid * B_NODE[lat]
+    achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
+    traffic, tnote = committed_traffic(args.workload, arith_name)
+    tiling_stats = {"n_ftiles": int(tiling.n_ftiles), "n_tiles": int(tiling.n_tiles),
+                    "phi": n_fluid / mask.size,
+                    "phi_t": n_fluid / (tiling.n_ftiles * a ** (3 if lat == 19 else 2))}
+    line = {
+        "metric": "D3Q19 sparse MLUPS + % HBM roofline" if lat == 19 else "D2Q9 sparse MLUPS + % HBM roofline",
+        "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": f"D{3 if lat == 19 else 2}Q{lat}",
+                   "size": list(mask.shape[::-1]), "tile": a, "fluid_nodes": n_fluid, **tiling_stats,
+                   "tau": params["tau"], "force": params["force"], "storage": "f64", "arith": arith_name,
+                   "stats_every": STATS_EVERY, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (two PDF copies of "
+                         f"{tiling.pdf_bytes / 1e9:.2f} GB each, L2 129 MB)",
+                   "geometry": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "k_step (tiled stream+collide)", "bytes_per_launch": bytes_per_launch,
+                     "step_kernel_ms": step_ms, "traffic_note": tnote},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "model_overheads": pm.predictions(lat, 8, a, 3 if lat == 19 else 2, tiling_stats["phi"],
+                                          tiling_stats["phi_t"],
+                                          tiling.n_tiles / max(1, tiling.n_ftiles)),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mask, params)
+    print(json.dumps(line))
+
+
+def run_e2e(mask, params, steps, arith, dev, world):
+    """Same metric through the C ABI from host buffers: pinned host mask ->
+    lbm_init (tiling + upload + equilibrium fill), the timed steps with the
+    stats read back every 100 steps, and rho/u fields back to host memory."""
+    import torch
+
+    from paper_1703_08015_gb300 import lbm
+
+    lat, a = params["lattice"], params["tile_a"]
+    p = lbm.make_params(lat, mask.shape, a, params["periodic"], params["tau"], params["force"], arith=arith)
+    info, _, _ = lbm.lbm_build_tilemap(p, mask, want_map=False, want_nbr=False)
+    nbytes = max(int(info.pdf_bytes), 256)
+    bufs = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    host_mask = torch.from_numpy(np.ascontiguousarray(mask)).pin_memory()
+    d = 3 if lat == 19 else 2
+    rho = torch.empty(mask.shape, dtype=torch.float64).pin_memory()
+    u = torch.empty((d,) + mask.shape, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    s = ctypes_stream(stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ctx = lbm.lbm_init(p, host_mask.numpy(), bufs[0], bufs[1], nbytes, None, None, s)
+    left = steps
+    n_stats = 0
+    while left > 0:
+        k = min(STATS_EVERY, left)
+        lbm.lbm_step(ctx, k, s)
+        left -= k
+        st = lbm.lbm_stats()
+        lbm.lbm_moments(ctx, None, None, st, 0, s)
+        n_stats += 1
+    lbm.lbm_moments(ctx, rho.numpy(), u.numpy(), None, 0, s)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    lbm.lbm_free(ctx)
+    words = (a ** (3 if lat == 19 else 2) + 63) // 64
+    h2d = int(info.n_ftiles) * (int(info.nbr_per_tile) * 4 + words * 8 + 12)  # tile tables uploaded
+    d2h = rho.numel() * 8 + u.numel() * 8 + n_stats * 64
+    return {"value": int(info.n_fluid) * steps * world / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "seconds": dt, "includes": "host tiling, table upload, equilibrium fill, steps, stats, rho/u readback"}
+
+
+def ctypes_stream(stream):
+    import ctypes
+
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

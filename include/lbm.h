@@ -1,0 +1,213 @@
+/*
+ * lbm.h -- C ABI of the GB300 sparse-geometry lattice Boltzmann library.
+ *
+ * One time step of the BGK lattice Boltzmann method (D2Q9, D3Q19) over a
+ * uniform mesh of fixed-size tiles of which only the non-empty ones are
+ * stored; every tile's fused stream+collide gathers its halo PDFs from its
+ * neighbour tiles through a tile-index map.  This is the "tiles with two
+ * copies" (T2C) method of Tomczak & Szafran, arXiv:1703.08015 (Sec. 3 and
+ * Fig. 5), written for sm_103a.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: LBM_OK (0) or a negative
+ *     LBM_ERR_* code.  No function aborts the process or traps the GPU.
+ *     lbm_last_error() returns a message for the calling host thread.
+ *   - Host masks and dense fields are laid out [z][y][x] with x fastest;
+ *     2D lattices use nz = 1.  mask[n] != 0 marks a fluid node.
+ *   - Dense PDF arrays are [i][z][y][x] (direction i slowest) in FP64 and
+ *     hold post-collision values; the link order is the one documented at
+ *     LBM_D2Q9 / LBM_D3Q19 below.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     stream-ordered; a context must not be used from two host threads at
+ *     once.
+ *   - The two device PDF buffers are allocated and freed by the caller (for
+ *     example as PyTorch tensors) and only borrowed by the library; the small
+ *     tables (tile masks, neighbour records, coordinates, reduction partials)
+ *     are allocated by lbm_init and released by lbm_free.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBM_OK            0
+#define LBM_ERR_ARG      (-1) /* bad argument: NULL pointer, size, lattice, tau <= 1/2 */
+#define LBM_ERR_SHAPE    (-2) /* a periodic axis is not a multiple of tile_a */
+#define LBM_ERR_CUDA     (-3) /* a CUDA runtime call failed */
+#define LBM_ERR_OOM      (-4) /* a device allocation failed */
+#define LBM_ERR_DIVERGED (-5) /* the mass or momentum sum is not finite */
+#define LBM_ERR_TIMEOUT  (-6) /* a bounded device-side wait ran out */
+#define LBM_ERR_BOUNDS   (-7) /* a checked kernel saw an index outside its buffers */
+#define LBM_ERR_CAPACITY (-8) /* a request exceeds a fixed capacity */
+
+/* ---- lattices ----------------------------------------------------------
+ * LBM_D2Q9  links: 0 (0,0); 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1);
+ *                  5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1).
+ *           weights 4/9, 1/9 (links 1-4), 1/36 (links 5-8).
+ * LBM_D3Q19 links: 0 (0,0,0); 1 +x 2 -x 3 +y 4 -y 5 +z 6 -z;
+ *                  7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0)
+ *                  11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1)
+ *                  15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1).
+ *           weights 1/3, 1/18 (links 1-6), 1/36 (links 7-18).
+ * The paper names both lattices (Fig. 1, Sec. 2.2) without printing either
+ * table; these are the standard sets. */
+#define LBM_D2Q9   9
+#define LBM_D3Q19 19
+
+/* Equilibrium model: Eq. 3 with Eq. 5 (quasi-compressible) or Eq. 4 with
+ * Eq. 6 (incompressible). */
+#define LBM_QUASI_COMPRESSIBLE 0
+#define LBM_INCOMPRESSIBLE     1
+
+/* PDF storage in device memory.  LBM_STORE_F64 is the FP64 method of the
+ * paper (all of its runs are double precision, Sec. 4). */
+#define LBM_STORE_F64  0
+#define LBM_STORE_F32  1 /* FP32 values, FP32 collision (not in the paper) */
+#define LBM_STORE_F16S 2 /* FP16 scaled deviations (f_i - w_i) * S, FP32 collision (not in the paper) */
+
+/* Arithmetic of the FP64 step.  Both variants compute the same update; they
+ * differ only in rounding (see lbm_step). */
+#define LBM_ARITH_AUTO   0 /* = LBM_ARITH_FIXED */
+#define LBM_ARITH_F64    1 /* native FP64 instructions */
+#define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions;
+                              nodes outside its range fall back to FP64 */
+
+/* lbm_moments flags */
+#define LBM_OUT_DEVICE    1 /* rho/u/pdf pointers are device pointers (default: host) */
+#define LBM_STATS_RESIDUAL 2 /* compute the steady-state residual against the
+                                velocity saved by the previous residual call,
+                                then save the current velocity */
+
+typedef struct lbm_params {
+    int lattice;      /* LBM_D2Q9 or LBM_D3Q19 */
+    int model;        /* LBM_QUASI_COMPRESSIBLE or LBM_INCOMPRESSIBLE */
+    int nx, ny, nz;   /* lattice size; nz = 1 for D2Q9 */
+    int tile_a;       /* nodes per tile edge a (Sec. 3): D2Q9 8, 16, 32; D3Q19 4, 8 */
+    int periodic[3];  /* per axis: 1 = periodic (length must be a multiple of a),
+                         0 = solid wall halfway outside the last node row */
+    double tau;       /* BGK relaxation time (Eq. 2), > 1/2; viscosity (tau - 1/2)/3 */
+    double force[3];  /* body-force density F (Guo forcing; not in the paper) */
+    double rho0;      /* density of the rest start (used when no rho field is given) */
+    int storage;      /* LBM_STORE_* */
+    int arith;        /* LBM_ARITH_* (LBM_STORE_F64 only) */
+    double f16_scale; /* LBM_STORE_F16S: scale S of the deviations; 0 = default 2^14 */
+} lbm_params;
+
+typedef struct lbm_tiling {
+    int32_t ntx, nty, ntz; /* tile mesh (ntz = 1 in 2D) */
+    int32_t n_tiles;       /* N_tiles = ntx * nty * ntz (Sec. 3.1.1.1) */
+    int32_t n_ftiles;      /* N_ftiles, the non-empty tiles */
+    int32_t nbr_per_tile;  /* 3^d entries in each neighbour record */
+    int64_t n_fluid;       /* N_fnodes, non-solid nodes (Eq. 11) */
+    size_t pdf_bytes;      /* bytes of ONE PDF copy in the requested storage */
+} lbm_tiling;
+
+typedef struct lbm_stats {
+    double mass;        /* sum over fluid nodes of rho */
+    double momentum[3]; /* sum over fluid nodes of rho u (u with the F/2 correction) */
+    double u2;          /* sum over fluid nodes of |u|^2 */
+    double du2;         /* sum of |u - u_saved|^2 (LBM_STATS_RESIDUAL) */
+    double residual;    /* sqrt(du2 / u2); +inf when no velocity was saved yet */
+    int64_t n_fluid;    /* fluid nodes summed */
+    int64_t step;       /* time steps taken since lbm_init */
+} lbm_stats;
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library */
+
+/* Tile the geometry (Sec. 3): cover it with a x a (x a) tiles starting at
+ * node (0,0), pad with solid nodes, drop the tiles that hold only solid
+ * nodes, and number the others by their rank in row-major scan order
+ * (x fastest).  Host only, no device work.
+ *   p         lattice, nx, ny, nz, tile_a, periodic and storage are read.
+ *   mask      host, nx*ny*nz bytes, [z][y][x], nonzero = fluid.
+ *   tile_map  host out, n_tiles int32 [tz][ty][tx]: the tile's index or -1
+ *             for a removed tile (the tileMap of Sec. 3); NULL = size query.
+ *   nbr       host out, n_ftiles * 3^d int32: for each non-empty tile the
+ *             index of each surrounding tile, offsets (dz, dy, dx) in
+ *             {-1,0,1} with dx fastest, -1 for a removed tile or one beyond
+ *             a non-periodic edge (the 3^3 tile bitmap of Fig. 5); NULL =
+ *             not wanted.  Its size is only known after a size query.
+ *   out       host out, the counts and the bytes of one PDF copy.
+ * Errors: LBM_ERR_ARG (NULL mask/out/p, bad sizes or tile edge),
+ * LBM_ERR_SHAPE (periodic axis not a multiple of tile_a). */
+int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask,
+                      int32_t* tile_map, int32_t* nbr, lbm_tiling* out);
+
+/* Create a context: tile the mask, upload the tile tables, and fill PDF copy
+ * A with the equilibrium f^eq(rho, u) of Eq. 3 (Eq. 4 for the incompressible
+ * model) at every fluid node, zero elsewhere.
+ *   out        receives the context (NULL on failure).
+ *   mask       host, as in lbm_build_tilemap.
+ *   pdf_a/b    device, caller-owned, each at least `pdf_bytes` bytes and
+ *              256-byte aligned; they must stay allocated until lbm_free.
+ *   rho_init   host, dense nx*ny*nz doubles, or NULL for rho0 everywhere.
+ *   u_init     host, dense 3 * nx*ny*nz doubles [component][z][y][x], or
+ *              NULL for rest.
+ *   stream     cudaStream_t on which the uploads and the fill run; the call
+ *              returns after they have been issued (tables copied from host
+ *              memory synchronously).
+ * Errors: LBM_ERR_ARG, LBM_ERR_SHAPE, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
+             void* pdf_a, void* pdf_b, size_t pdf_bytes,
+             const double* rho_init, const double* u_init, void* stream);
+
+/* Advance `nsteps` time steps of Eq. 7 with the Eq. 2 BGK collision: each
+ * non-empty tile gathers the post-collision values f*_i(r - c_i) of its own
+ * and its neighbour tiles through the neighbour record (Fig. 5), takes its
+ * own f*_{opp(i)}(r) where r - c_i is solid, empty or beyond a wall
+ * (propagation only between non-solid nodes, Sec. 3.2: halfway bounce-back),
+ * collides, and stores into the other copy; the copies then swap (Sec. 3).
+ * Asynchronous on `stream`.  With LBM_ARITH_FIXED the FP64 update is computed
+ * with 64-bit fixed-point integers (resolution 2^-60) and rounded once to
+ * FP64; it agrees with LBM_ARITH_F64 to rounding.
+ * Errors: LBM_ERR_ARG (NULL ctx, nsteps < 0), LBM_ERR_CUDA. */
+int lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
+
+/* Density and velocity that the next step will collide with (the gathered
+ * values; rho = sum f_i, u from Eq. 5 / Eq. 6 with the F/2 correction), and
+ * FP64 reductions over the fluid nodes in a fixed order (deterministic).
+ *   rho    dense nx*ny*nz doubles or NULL; solid nodes get NaN.
+ *   u      dense 3*nx*ny*nz doubles [component][z][y][x] or NULL; NaN at solid.
+ *   stats  host, or NULL.
+ *   flags  LBM_OUT_DEVICE: rho and u are device pointers (default host);
+ *          LBM_STATS_RESIDUAL: fill stats->du2 and stats->residual.
+ * Synchronises `stream` when anything is returned to host memory.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_DIVERGED (mass or momentum not
+ * finite; stats is still filled). */
+int lbm_moments(lbm_ctx* ctx, double* rho, double* u, lbm_stats* stats,
+                int flags, void* stream);
+
+/* Copy the current post-collision PDFs out as a dense FP64 array
+ * [i][z][y][x] (q * nx*ny*nz doubles; solid nodes NaN), host or device
+ * (LBM_OUT_DEVICE).  Used for checkpoints and for checking the step.
+ * Synchronises `stream` for host output.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_export_pdfs(lbm_ctx* ctx, double* pdfs, int flags, void* stream);
+
+/* Overwrite the current post-collision PDFs from a dense FP64 array laid out
+ * as in lbm_export_pdfs (values at solid nodes are ignored); `step` becomes
+ * the context's step count.  Resuming from an exported state reproduces an
+ * uninterrupted run bit for bit.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
+                    void* stream);
+
+/* Counts of the context's tiling (see lbm_tiling).  Errors: LBM_ERR_ARG. */
+int lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out);
+
+/* Release the context and the tables lbm_init allocated (never the caller's
+ * PDF buffers).  Waits for the context's pending work.  NULL is accepted. */
+int lbm_free(lbm_ctx* ctx);
+
+/* Message describing the last failure on the calling host thread. */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,106 @@
+// internal.h -- host-side declarations shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---- errors ---------------------------------------------------------------
+int fail(int code, const char* fmt, ...);          // records a message, returns code
+int cuda_fail(cudaError_t e, const char* what);    // LBM_ERR_CUDA or LBM_ERR_OOM
+
+#define LBM_CUDA_TRY(call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::lbm::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---- host tiling ------------------------------------------------------------
+struct HostTiling {
+    lbm_tiling info{};
+    int a = 0, d = 0, nn = 0, words = 0;     // edge, dimension, 3^d, mask words per tile
+    std::vector<int32_t> tile_map;           // [n_tiles]
+    std::vector<int32_t> nbr;                // [n_ftiles][nn]
+    std::vector<uint64_t> tmask;             // [n_ftiles][words], bit n = node n fluid
+    std::vector<int32_t> coords;             // [n_ftiles][3] tile coordinates
+};
+int validate_params(const lbm_params* p);
+int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out);
+int lattice_q(int lattice);
+size_t bytes_per_value(int storage);
+
+// ---- kernel arguments --------------------------------------------------------
+// Constants of the fixed-point FP64 path (all values scaled by 2^60).
+struct FixedConsts {
+    long long k_keep;       // (1 - omega) * 2^62: weight of the pre-collision value
+    long long k_rho[3];     // omega * w_c * 2^62 per weight class
+    long long k_j[3];       // 3 * omega * w_c * 2^62 per weight class
+    long long k_q[3];       // omega * w_c * 2^62 (scales the quadratic term)
+    long long half_f[3];    // F/2 in units of 2^-60
+    long long s_odd[19];    // (1 - omega/2) w_i 3 c_i.F in units of 2^-60
+    long long k_force;      // (1 - omega/2) * 2^62
+    long long f_sc[3];      // F * 2^60 for the quadratic forcing part
+    long long w_bits[3];    // bit patterns of the weights w_c (FP64)
+    long long wsum_fix;     // sum_i w_i (exact) in units of 2^-60
+};
+
+struct StepArgs {
+    const void* src;
+    void* dst;
+    const int32_t* nbr;
+    const uint64_t* tmask;
+    int n_tiles;
+    double omega;         // 1 / tau
+    double tau;
+    double force[3];
+    double f16_scale;     // storage scale for LBM_STORE_F16S
+    double f16_inv_scale;
+    float omega_f, force_f[3], f16_scale_f, f16_inv_scale_f;
+    int* err;             // device error word (0 = none)
+    FixedConsts fx;
+};
+
+struct NodeArgs {         // kernels that visit every node of every tile
+    const void* pdf;      // current copy
+    void* pdf_out;        // second copy (init writes both)
+    const int32_t* nbr;
+    const uint64_t* tmask;
+    const int32_t* coords;
+    int n_tiles;
+    int nx, ny, nz;
+    double force[3];
+    double rho0;
+    double f16_scale, f16_inv_scale;
+    const double* rho_in;     // dense or NULL
+    const double* u_in;       // dense [3][N] or NULL
+    double* rho_out;          // dense or NULL
+    double* u_out;            // dense [3][N] or NULL
+    double* dense_pdf;        // dense [q][N]
+    const double* dense_pdf_in;
+    double* u_saved;          // [n_tiles][3][NT] or NULL
+    int residual;             // compare and save velocity
+    double* partials;         // [blocks][8]
+};
+
+using StepLaunch = cudaError_t (*)(const StepArgs&, cudaStream_t);
+using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
+
+// Kernel selection (nullptr when a combination is not compiled).
+StepLaunch select_step(int lattice, int a, int model, int storage, int arith);
+NodeLaunch select_init(int lattice, int a, int model, int storage);
+NodeLaunch select_moments(int lattice, int a, int model, int storage);
+NodeLaunch select_export(int lattice, int a, int storage);
+NodeLaunch select_import(int lattice, int a, int storage);
+int node_blocks(int lattice, int a, int n_tiles);  // grid of the node kernels
+cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
+cudaError_t launch_reduce(const double* partials, int nblocks, double* result, cudaStream_t s);
+
+void fixed_consts(const lbm_params* p, FixedConsts* k);
+
+}  // namespace lbm

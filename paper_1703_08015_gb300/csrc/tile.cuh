@@ -1,0 +1,136 @@
+// tile.cuh -- device side of the tiled step: staging of a tile's
+// neighbourhood in shared memory and the gather (streaming) of Fig. 5.
+//
+// One thread owns one node of one tile (row order, Sec. 3.2); TPB tiles share
+// a thread block.  Before the single barrier, the threads of a tile copy the
+// tile's 3^d neighbour record into shared memory as base pointers of the
+// neighbours' PDF blocks, together with the neighbours' fluid-node bit masks
+// (Fig. 5, steps 1-3: the tile bitmap and the node types of the tile and its
+// halo).  After the barrier every fluid node pulls f*_i(r - c_i) from the
+// tile that holds r - c_i, or, when that node is solid, in a removed tile or
+// beyond a wall, its own f*_{opp(i)}(r) (halfway bounce-back).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+
+template <class TL, int TPB>
+struct NeighShared {
+    const unsigned char* base[TPB][TL::NN];  // PDF block of each neighbour slot
+    uint64_t m[TPB][TL::NN][TL::W];          // its fluid-node bits (0 when removed)
+};
+
+// Threads of one tile cooperatively stage the neighbourhood of `tile`.
+template <class TL, int TPB>
+__device__ __forceinline__ void stage_neighbourhood(NeighShared<TL, TPB>& sh, const int32_t* __restrict__ nbr,
+                                                    const uint64_t* __restrict__ tmask,
+                                                    const unsigned char* pdf, size_t tile_bytes, int n_tiles,
+                                                    int tile, int lt, int node) {
+    for (int k = node; k < TL::NN * TL::W; k += TL::NT) {
+        const int slot = k / TL::W, w = k - slot * TL::W;
+        const int nb = tile < n_tiles ? __ldg(nbr + (size_t)tile * TL::NN + slot) : -1;
+        sh.m[lt][slot][w] = nb >= 0 ? __ldg(tmask + (size_t)nb * TL::W + w) : 0ull;
+        if (w == 0) sh.base[lt][slot] = pdf + (size_t)(nb >= 0 ? nb : 0) * tile_bytes;
+    }
+}
+
+template <class TL, int TPB>
+__device__ __forceinline__ bool mask_bit(const NeighShared<TL, TPB>& sh, int lt, int slot, int n) {
+    if constexpr (TL::W == 1)
+        return (sh.m[lt][slot][0] >> n) & 1ull;
+    else
+        return (sh.m[lt][slot][n >> 6] >> (n & 63)) & 1ull;
+}
+
+template <int A>
+struct NodePos {
+    int lx, ly, lz;
+};
+
+template <class TL>
+__device__ __forceinline__ NodePos<(1 << TL::LA)> node_pos(int node) {
+    constexpr int A = 1 << TL::LA;
+    NodePos<A> p;
+    p.lx = node & (A - 1);
+    p.ly = (node >> TL::LA) & (A - 1);
+    p.lz = TL::D == 3 ? node >> (2 * TL::LA) : 0;
+    return p;
+}
+
+// Source of the pull along link I: the neighbour slot and node index that
+// hold r - c_I.
+template <class L, int A, int I>
+struct PullSource {
+    using TL = Tile<L, A>;
+    using K = Link<L, I>;
+    int slot, sn;
+    __device__ __forceinline__ PullSource(const NodePos<A>& p) {
+        const int sx = p.lx - K::cx, sy = p.ly - K::cy, sz = p.lz - K::cz;
+        const int tx = K::cx > 0 ? -(sx < 0) : (K::cx < 0 ? (sx >= A) : 0);
+        const int ty = K::cy > 0 ? -(sy < 0) : (K::cy < 0 ? (sy >= A) : 0);
+        const int tz = K::cz > 0 ? -(sz < 0) : (K::cz < 0 ? (sz >= A) : 0);
+        slot = TL::CENTER + tx + 3 * ty + 9 * tz;
+        sn = (sx & (A - 1)) | ((sy & (A - 1)) << TL::LA) | ((sz & (A - 1)) << (2 * TL::LA));
+    }
+};
+
+// Gather the q post-collision words that arrive at `node` (raw storage words).
+template <class L, int A, int TPB, class T>
+__device__ __forceinline__ void gather(const NeighShared<Tile<L, A>, TPB>& sh, int lt, int node,
+                                       const NodePos<A>& p, T (&f)[L::Q]) {
+    using TL = Tile<L, A>;
+    const T* own = reinterpret_cast<const T*>(sh.base[lt][TL::CENTER]);
+    f[0] = __ldg(own + node);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const PullSource<L, A, i> s(p);
+        const bool fl = mask_bit(sh, lt, s.slot, s.sn);
+        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * TL::NT + s.sn
+                          : own + Link<L, i>::opp * TL::NT + node;
+        f[i] = __ldg(src);
+    });
+}
+
+// ---- storage policies: raw words <-> FP64 values ------------------------------
+struct StoreF64 {
+    using T = unsigned long long;
+    static constexpr int id = LBM_STORE_F64;
+    template <class L, int I>
+    __device__ static __forceinline__ double to_f64(T r, double) { return __longlong_as_double((long long)r); }
+    template <class L, int I>
+    __device__ static __forceinline__ T from_f64(double v, double) { return (T)__double_as_longlong(v); }
+};
+
+struct StoreF32 {
+    using T = unsigned int;
+    static constexpr int id = LBM_STORE_F32;
+    template <class L, int I>
+    __device__ static __forceinline__ double to_f64(T r, double) { return (double)__uint_as_float(r); }
+    template <class L, int I>
+    __device__ static __forceinline__ T from_f64(double v, double) { return __float_as_uint((float)v); }
+};
+
+// FP16 holding the scaled deviation (f_i - w_i) * scale.
+struct StoreF16S {
+    using T = unsigned short;
+    static constexpr int id = LBM_STORE_F16S;
+    template <class L, int I>
+    __device__ static __forceinline__ double to_f64(T r, double inv_scale) {
+        return Link<L, I>::w + (double)__half2float(__ushort_as_half(r)) * inv_scale;
+    }
+    template <class L, int I>
+    __device__ static __forceinline__ T from_f64(double v, double scale) {
+        return __half_as_ushort(__float2half_rn((float)((v - Link<L, I>::w) * scale)));
+    }
+};
+
+template <class L, int A>
+constexpr int tiles_per_block() {
+    return Tile<L, A>::NT >= 256 ? 1 : 256 / Tile<L, A>::NT;
+}
+
+}  // namespace lbm

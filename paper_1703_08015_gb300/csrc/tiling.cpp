@@ -1,0 +1,181 @@
+// tiling.cpp -- host-side tiling of a masked lattice (Sec. 3 of
+// Tomczak & Szafran, arXiv:1703.08015) and the lbm_build_tilemap entry point.
+//
+// The geometry is covered by a uniform mesh of a x a (x a) tiles anchored at
+// node (0,0); nodes beyond the lattice are solid padding; tiles with no fluid
+// node are removed.  A non-empty tile's index is its rank in row-major scan
+// order (x fastest), which is what the tileMap stores (-1 for removed tiles).
+// Each non-empty tile also gets the 3^d record of its neighbours' indices
+// (the local copy of the tile bitmap in Fig. 5) and a bit mask of its fluid
+// nodes (one bit per node instead of the paper's s_t = 2 bytes, Eq. 21).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace lbm {
+
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky-free error so the context stays usable
+    fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s (%s)", what,
+         cudaGetErrorString(e), cudaGetErrorName(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+int lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q19 ? 19 : 0; }
+
+size_t bytes_per_value(int storage) {
+    switch (storage) {
+        case LBM_STORE_F64: return 8;
+        case LBM_STORE_F32: return 4;
+        case LBM_STORE_F16S: return 2;
+        default: return 0;
+    }
+}
+
+static bool tile_edge_ok(int lattice, int a) {
+    if (lattice == LBM_D2Q9) return a == 8 || a == 16 || a == 32;
+    if (lattice == LBM_D3Q19) return a == 4 || a == 8;
+    return false;
+}
+
+int validate_params(const lbm_params* p) {
+    if (!p) return fail(LBM_ERR_ARG, "params is NULL");
+    if (!lattice_q(p->lattice)) return fail(LBM_ERR_ARG, "unknown lattice %d", p->lattice);
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_ERR_ARG, "lattice size must be positive");
+    if (p->lattice == LBM_D2Q9 && p->nz != 1) return fail(LBM_ERR_ARG, "D2Q9 needs nz == 1");
+    if (!tile_edge_ok(p->lattice, p->tile_a))
+        return fail(LBM_ERR_ARG, "tile edge %d not supported for lattice %d", p->tile_a, p->lattice);
+    if (!bytes_per_value(p->storage)) return fail(LBM_ERR_ARG, "unknown storage %d", p->storage);
+    if (p->model != LBM_QUASI_COMPRESSIBLE && p->model != LBM_INCOMPRESSIBLE)
+        return fail(LBM_ERR_ARG, "unknown model %d", p->model);
+    const int d = p->lattice == LBM_D2Q9 ? 2 : 3;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int ax = 0; ax < d; ax++)
+        if (p->periodic[ax] && n[ax] % p->tile_a != 0)
+            return fail(LBM_ERR_SHAPE, "periodic axis %d of length %d is not a multiple of %d", ax,
+                        n[ax], p->tile_a);
+    return LBM_OK;
+}
+
+int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    if (!mask) return fail(LBM_ERR_ARG, "mask is NULL");
+    const int a = p->tile_a;
+    const int d = p->lattice == LBM_D2Q9 ? 2 : 3;
+    const int az = d == 3 ? a : 1;
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const int ntx = (nx + a - 1) / a, nty = (ny + a - 1) / a, ntz = d == 3 ? (nz + a - 1) / a : 1;
+    const int64_t n_tiles64 = (int64_t)ntx * nty * ntz;
+    if (n_tiles64 > INT32_MAX) return fail(LBM_ERR_CAPACITY, "too many tiles");
+    const int nt = a * a * az;
+    T->a = a;
+    T->d = d;
+    T->nn = d == 3 ? 27 : 9;
+    T->words = (nt + 63) / 64;
+    T->tile_map.assign((size_t)n_tiles64, -1);
+    T->nbr.clear();
+    T->tmask.clear();
+    T->coords.clear();
+
+    int32_t count = 0;
+    int64_t n_fluid = 0;
+    std::vector<uint64_t> bits(T->words);
+    for (int tz = 0; tz < ntz; tz++)
+        for (int ty = 0; ty < nty; ty++)
+            for (int tx = 0; tx < ntx; tx++) {
+                std::fill(bits.begin(), bits.end(), 0ull);
+                int nf = 0;
+                for (int lz = 0; lz < az; lz++) {
+                    const int z = tz * az + lz;
+                    if (z >= nz) break;
+                    for (int ly = 0; ly < a; ly++) {
+                        const int y = ty * a + ly;
+                        if (y >= ny) break;
+                        const uint8_t* row = mask + ((size_t)z * ny + y) * nx;
+                        for (int lx = 0; lx < a; lx++) {
+                            const int x = tx * a + lx;
+                            if (x >= nx) break;
+                            if (row[x]) {
+                                const int node = lx + a * (ly + a * lz);
+                                bits[node >> 6] |= 1ull << (node & 63);
+                                nf++;
+                            }
+                        }
+                    }
+                }
+                if (nf) {
+                    T->tile_map[((size_t)tz * nty + ty) * ntx + tx] = count++;
+                    T->tmask.insert(T->tmask.end(), bits.begin(), bits.end());
+                    T->coords.push_back(tx);
+                    T->coords.push_back(ty);
+                    T->coords.push_back(tz);
+                    n_fluid += nf;
+                }
+            }
+
+    const int per[3] = {p->periodic[0] ? 1 : 0, p->periodic[1] ? 1 : 0, d == 3 && p->periodic[2] ? 1 : 0};
+    const int ntv[3] = {ntx, nty, ntz};
+    T->nbr.resize((size_t)count * T->nn);
+    for (int32_t k = 0; k < count; k++) {
+        const int* c = &T->coords[(size_t)3 * k];
+        int slot = 0;
+        for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++, slot++) {
+                    int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                    bool ok = true;
+                    for (int ax = 0; ax < 3; ax++) {
+                        if (q[ax] < 0 || q[ax] >= ntv[ax]) {
+                            if (per[ax])
+                                q[ax] = (q[ax] + ntv[ax]) % ntv[ax];
+                            else
+                                ok = false;
+                        }
+                    }
+                    T->nbr[(size_t)k * T->nn + slot] =
+                        ok ? T->tile_map[((size_t)q[2] * nty + q[1]) * ntx + q[0]] : -1;
+                }
+    }
+
+    lbm_tiling& I = T->info;
+    I.ntx = ntx;
+    I.nty = nty;
+    I.ntz = ntz;
+    I.n_tiles = (int32_t)n_tiles64;
+    I.n_ftiles = count;
+    I.nbr_per_tile = T->nn;
+    I.n_fluid = n_fluid;
+    I.pdf_bytes = (size_t)count * lattice_q(p->lattice) * nt * bytes_per_value(p->storage);
+    return LBM_OK;
+}
+
+}  // namespace lbm
+
+extern "C" int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask, int32_t* tile_map,
+                                 int32_t* nbr, lbm_tiling* out) {
+    using namespace lbm;
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    HostTiling T;
+    int rc = build_tiling(p, mask, &T);
+    if (rc) return rc;
+    *out = T.info;
+    if (tile_map) std::memcpy(tile_map, T.tile_map.data(), T.tile_map.size() * sizeof(int32_t));
+    if (nbr) std::memcpy(nbr, T.nbr.data(), T.nbr.size() * sizeof(int32_t));
+    return LBM_OK;
+}
+
+extern "C" const char* lbm_last_error(void) { return lbm::g_err; }

@@ -233,6 +233,10 @@ def workload(name: str, seed: int = None):
         mask, info = sphere_pack_3d(256, seed=2 if seed is None else seed)
         params = dict(lattice=19, tile_a=4, periodic=(1, 0, 0), tau=0.6,
                       force=(1e-6, 0.0, 0.0), rho0=1.0, steps=2000)
+    elif name == "d3q19_spheres_128":
+        mask, info = sphere_pack_3d(128, seed=2 if seed is None else seed)
+        params = dict(lattice=19, tile_a=4, periodic=(1, 0, 0), tau=0.6,
+                      force=(1e-6, 0.0, 0.0), rho0=1.0, steps=2000)
     elif name == "d3q19_tubes_256":
         mask, info = tube_tree_3d(256, seed=3 if seed is None else seed)
         params = dict(lattice=19, tile_a=4, periodic=(1, 0, 0), tau=0.6,

@@ -1,0 +1,242 @@
+"""Python binding of the C ABI in include/lbm.h (argument marshalling only).
+
+The functions below carry the C names and forward to the in-tree CUDA library
+``_build/libpaper_lbm.so``; every step of the method runs in its kernels.
+PyTorch supplies device memory (the two PDF copies) and the CUDA stream.
+There is no CPU fallback: if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+LBM_OK = 0
+ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_SHAPE", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_OOM",
+          -5: "LBM_ERR_DIVERGED", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_BOUNDS", -8: "LBM_ERR_CAPACITY"}
+LBM_D2Q9, LBM_D3Q19 = 9, 19
+LBM_QUASI_COMPRESSIBLE, LBM_INCOMPRESSIBLE = 0, 1
+LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S = 0, 1, 2
+LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED = 0, 1, 2
+LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
+
+EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
+            "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("model", ctypes.c_int), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("tile_a", ctypes.c_int),
+                ("periodic", ctypes.c_int * 3), ("tau", ctypes.c_double),
+                ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("storage", ctypes.c_int),
+                ("arith", ctypes.c_int), ("f16_scale", ctypes.c_double)]
+
+
+class lbm_tiling(ctypes.Structure):
+    _fields_ = [("ntx", ctypes.c_int32), ("nty", ctypes.c_int32), ("ntz", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int32), ("n_ftiles", ctypes.c_int32),
+                ("nbr_per_tile", ctypes.c_int32), ("n_fluid", ctypes.c_int64),
+                ("pdf_bytes", ctypes.c_size_t)]
+
+
+class lbm_stats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("u2", ctypes.c_double),
+                ("du2", ctypes.c_double), ("residual", ctypes.c_double), ("n_fluid", ctypes.c_int64),
+                ("step", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library(build: bool = True):
+    """Load the CUDA library (building it in-tree first when `build`)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            P, I = ctypes.c_void_p, ctypes.c_int
+            lib.lbm_build_tilemap.argtypes = [ctypes.POINTER(lbm_params), P, P, P, ctypes.POINTER(lbm_tiling)]
+            lib.lbm_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(lbm_params), P, P, P,
+                                     ctypes.c_size_t, P, P, P]
+            lib.lbm_step.argtypes = [P, I, P]
+            lib.lbm_moments.argtypes = [P, P, P, ctypes.POINTER(lbm_stats), I, P]
+            lib.lbm_export_pdfs.argtypes = [P, P, I, P]
+            lib.lbm_import_pdfs.argtypes = [P, P, ctypes.c_int64, I, P]
+            lib.lbm_get_tiling.argtypes = [P, ctypes.POINTER(lbm_tiling)]
+            lib.lbm_free.argtypes = [P]
+            lib.lbm_last_error.restype = ctypes.c_char_p
+            for name in EXPORTED:
+                getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+            lib.lbm_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        raise LBMError(rc, lbm_last_error())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lbm_last_error() -> str:
+    return library().lbm_last_error().decode()
+
+
+def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0, 0.0, 0.0),
+                rho0=1.0, model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64,
+                arith=LBM_ARITH_AUTO, f16_scale=0.0) -> lbm_params:
+    """lbm_params from a mask shape (nz, ny, nx) or (ny, nx)."""
+    if len(shape) == 2:
+        shape = (1,) + tuple(shape)
+    nz, ny, nx = shape
+    p = lbm_params()
+    p.lattice, p.model, p.nx, p.ny, p.nz, p.tile_a = lattice, model, nx, ny, nz, tile_a
+    for k in range(3):
+        p.periodic[k] = int(bool(periodic[k])) if k < len(periodic) else 0
+        p.force[k] = float(force[k]) if k < len(force) else 0.0
+    p.tau, p.rho0, p.storage, p.arith, p.f16_scale = float(tau), float(rho0), storage, arith, float(f16_scale)
+    return p
+
+
+def lbm_build_tilemap(params: lbm_params, mask, want_map=True, want_nbr=True):
+    """Returns (lbm_tiling, tile_map[ntz,nty,ntx] or None, nbr[n_ftiles,3^d] or None)."""
+    lib = library()
+    m = np.ascontiguousarray(mask, np.uint8)
+    info = lbm_tiling()
+    _check(lib.lbm_build_tilemap(ctypes.byref(params), _ptr(m), None, None, ctypes.byref(info)))
+    tm = np.empty((info.ntz, info.nty, info.ntx), np.int32) if want_map else None
+    nb = np.empty((info.n_ftiles, info.nbr_per_tile), np.int32) if want_nbr else None
+    if want_map or want_nbr:
+        _check(lib.lbm_build_tilemap(ctypes.byref(params), _ptr(m), _ptr(tm), _ptr(nb), ctypes.byref(info)))
+    return info, tm, nb
+
+
+def lbm_init(params: lbm_params, mask, pdf_a, pdf_b, pdf_bytes, rho_init=None, u_init=None, stream=None):
+    """Returns an opaque context handle (ctypes.c_void_p)."""
+    lib = library()
+    ctx = ctypes.c_void_p()
+    m = np.ascontiguousarray(mask, np.uint8)
+    r = None if rho_init is None else np.ascontiguousarray(rho_init, np.float64)
+    u = None if u_init is None else np.ascontiguousarray(u_init, np.float64)
+    _check(lib.lbm_init(ctypes.byref(ctx), ctypes.byref(params), _ptr(m), _ptr(pdf_a), _ptr(pdf_b),
+                        pdf_bytes, _ptr(r), _ptr(u), stream))
+    return ctx
+
+
+def lbm_step(ctx, nsteps, stream=None):
+    return _check(library().lbm_step(ctx, int(nsteps), stream))
+
+
+def lbm_moments(ctx, rho=None, u=None, stats=None, flags=0, stream=None):
+    """Fills rho/u (numpy host arrays or device tensors with LBM_OUT_DEVICE) and
+    stats (lbm_stats); returns the status (LBM_ERR_DIVERGED is not raised)."""
+    rc = library().lbm_moments(ctx, _ptr(rho), _ptr(u), None if stats is None else ctypes.byref(stats),
+                               int(flags), stream)
+    if rc not in (LBM_OK, -5):
+        _check(rc)
+    return rc
+
+
+def lbm_export_pdfs(ctx, out, flags=0, stream=None):
+    return _check(library().lbm_export_pdfs(ctx, _ptr(out), int(flags), stream))
+
+
+def lbm_import_pdfs(ctx, pdfs, step, flags=0, stream=None):
+    return _check(library().lbm_import_pdfs(ctx, _ptr(pdfs), int(step), int(flags), stream))
+
+
+def lbm_get_tiling(ctx) -> lbm_tiling:
+    info = lbm_tiling()
+    _check(library().lbm_get_tiling(ctx, ctypes.byref(info)))
+    return info
+
+
+def lbm_free(ctx):
+    return _check(library().lbm_free(ctx))
+
+
+class Solver:
+    """A context plus its two PDF copies held as PyTorch device tensors."""
+
+    def __init__(self, mask, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
+                 model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64, arith=LBM_ARITH_AUTO,
+                 f16_scale=0.0, rho_init=None, u_init=None, device="cuda"):
+        import torch
+
+        self.torch = torch
+        mask = np.asarray(mask, np.uint8)
+        if mask.ndim == 2:
+            mask = mask[None]
+        self.mask = np.ascontiguousarray(mask)
+        self.shape = self.mask.shape
+        self.q = lattice
+        self.params = make_params(lattice, self.shape, tile_a, periodic, tau, force, rho0, model, storage,
+                                  arith, f16_scale)
+        self.tiling, _, _ = lbm_build_tilemap(self.params, self.mask, want_map=False, want_nbr=False)
+        nbytes = max(int(self.tiling.pdf_bytes), 256)
+        self.device = torch.device(device)
+        self.pdf = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.stream = torch.cuda.current_stream(self.device)
+        self.ctx = lbm_init(self.params, self.mask, self.pdf[0], self.pdf[1], nbytes, rho_init, u_init,
+                            self._s())
+
+    def _s(self):
+        return ctypes.c_void_p(self.stream.cuda_stream)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n, self._s())
+
+    def moments(self, residual=False):
+        """(rho[nz,ny,nx], u[d,nz,ny,nx], lbm_stats, status) on the host."""
+        d = 3 if self.q == LBM_D3Q19 else 2
+        rho = np.empty(self.shape, np.float64)
+        u = np.empty((d,) + self.shape, np.float64)
+        st = lbm_stats()
+        rc = lbm_moments(self.ctx, rho, u, st, LBM_STATS_RESIDUAL if residual else 0, self._s())
+        return rho, u, st, rc
+
+    def stats(self, residual=False):
+        st = lbm_stats()
+        rc = lbm_moments(self.ctx, None, None, st, LBM_STATS_RESIDUAL if residual else 0, self._s())
+        return st, rc
+
+    def export_pdfs(self):
+        out = np.empty((self.q,) + self.shape, np.float64)
+        lbm_export_pdfs(self.ctx, out, 0, self._s())
+        return out
+
+    def import_pdfs(self, pdfs, step):
+        lbm_import_pdfs(self.ctx, np.ascontiguousarray(pdfs, np.float64), step, 0, self._s())
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

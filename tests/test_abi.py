@@ -1,0 +1,101 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point include/lbm.h declares, and its host tiling (lbm_build_tilemap, Sec. 3)
+matches the reference tiling bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import tilemap_ref as tr
+from paper_1703_08015_gb300 import geometry as geo
+from paper_1703_08015_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    lib = lbm.library()
+    declared = _declared()
+    assert {"lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_free"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def _check_tiling(mask, lattice, a, periodic):
+    p = lbm.make_params(lattice, mask.shape, a, periodic)
+    info, tm, nb = lbm.lbm_build_tilemap(p, mask)
+    dim = 2 if lattice == lbm.LBM_D2Q9 else 3
+    rtm, rnb, rmask, _ = tr.build_tilemap(mask, a, periodic, dim)
+    assert np.array_equal(tm, rtm)
+    assert np.array_equal(nb, rnb)
+    assert info.n_ftiles == rmask.shape[0]
+    assert info.n_tiles == rtm.size
+    assert info.n_fluid == int(np.count_nonzero(mask))
+    q = lattice
+    assert info.pdf_bytes == info.n_ftiles * q * a ** dim * 8
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tilemap_matches_reference(seed):
+    rng = np.random.default_rng(100 + seed)
+    if seed % 2:
+        a = int(rng.choice([8, 16, 32]))
+        shape = (1, int(rng.integers(5, 70)), a * int(rng.integers(1, 4)))
+        lattice = lbm.LBM_D2Q9
+        per = (1, int(rng.integers(0, 2)) if shape[1] % a == 0 else 0, 0)
+    else:
+        a = int(rng.choice([4, 8]))
+        shape = (int(rng.integers(3, 20)), int(rng.integers(3, 20)), a * int(rng.integers(1, 4)))
+        lattice = lbm.LBM_D3Q19
+        per = (1, 0, int(rng.integers(0, 2)) if shape[0] % a == 0 else 0)
+    mask = (rng.random(shape) < rng.uniform(0.02, 0.7)).astype(np.uint8)
+    _check_tiling(mask, lattice, a, per)
+
+
+def test_tilemap_workload_sphere_pack():
+    mask, _ = geo.sphere_pack_3d(shape=(64, 48, 40), seed=7)
+    _check_tiling(mask, lbm.LBM_D3Q19, 4, (1, 0, 0))
+
+
+def test_tilemap_edge_cases():
+    z = np.zeros((8, 8, 8), np.uint8)
+    p = lbm.make_params(lbm.LBM_D3Q19, z.shape, 4)
+    info, tm, nb = lbm.lbm_build_tilemap(p, z)
+    assert info.n_ftiles == 0 and np.all(tm == -1) and nb.shape == (0, 27) and info.pdf_bytes == 0
+    m = np.ones((4, 4, 10), np.uint8)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_build_tilemap(lbm.make_params(lbm.LBM_D3Q19, m.shape, 4, (1, 0, 0)), m)
+    assert e.value.code == -2
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_build_tilemap(lbm.make_params(lbm.LBM_D3Q19, m.shape, 5), m)
+    assert e.value.code == -1
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_build_tilemap(lbm.make_params(lbm.LBM_D2Q9, m.shape, 16), m)  # nz != 1
+    assert e.value.code == -1
+    one = np.zeros((1, 20, 20), np.uint8)
+    one[0, 17, 3] = 1
+    info, tm, nb = lbm.lbm_build_tilemap(lbm.make_params(lbm.LBM_D2Q9, one.shape, 16), one)
+    assert info.n_ftiles == 1 and tm.tolist() == [[[-1, -1], [0, -1]]]
+
+
+def test_null_arguments_are_rejected():
+    lib = lbm.library()
+    info = lbm.lbm_tiling()
+    assert lib.lbm_build_tilemap(None, None, None, None, ctypes.byref(info)) == -1
+    assert lib.lbm_step(None, 1, None) == -1
+    assert lib.lbm_moments(None, None, None, None, 0, None) == -1
+    assert lib.lbm_free(None) == 0
+    assert "NULL" in lbm.lbm_last_error() or lbm.lbm_last_error() != ""

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar: max relative error <= 1e-12 over every PDF of every fluid node after the
+stated number of steps (the tolerance the FP64 method is held to).  Small
+cases span several tiles plus a ragged tail (sizes that are not multiples of
+the tile edge); the full-size 3D workloads are checked on sampled nodes with a
+one-step comparison plus invariants that hold at any size.
+"""
+import numpy as np
+import pytest
+
+from paper_1703_08015_gb300 import geometry as geo
+from paper_1703_08015_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def max_rel(gpu, ref, mask):
+    fl = np.asarray(mask).astype(bool)
+    g = gpu[:, fl]
+    r = ref[:, fl]
+    assert np.all(np.isfinite(g))
+    return float(np.max(np.abs(g - r) / np.abs(r)))
+
+
+def run_both(oracle, mask, lattice, a, per, tau, F, steps, model=0, arith=lbm.LBM_ARITH_AUTO):
+    _cuda()
+    s = lbm.Solver(mask, lattice, a, per, tau, F, model=model, arith=arith)
+    try:
+        s.step(steps)
+        gpu = s.export_pdfs()
+    finally:
+        s.close()
+    ref = oracle.run(lattice, mask, per, tau, F, oracle.init(lattice, mask, model=model), steps, model=model)
+    return gpu, ref
+
+
+ARITHS = [lbm.LBM_ARITH_F64, lbm.LBM_ARITH_FIXED]
+
+
+def _small_cases():
+    m2, _ = geo.circles_2d(48, 35, seed=11, r_min=2, r_max=5, max_attempts=2000)
+    m3, _ = geo.sphere_pack_3d(shape=(24, 22, 18), seed=12, r_min=2, r_max=4, target_fluid=0.45)
+    m3b, _ = geo.tube_tree_3d(shape=(32, 20, 19), seed=13, r_min=1.5, r_max=3.0, target_fluid=0.12)
+    m2r = geo.random_mask(64, 40, 1, fluid=0.75, seed=14)
+    return [
+        ("d2q9_a16_circles", m2, 9, 16, (1, 0, 0), 0.8, (1e-5, 2e-6, 0), 300, 0),
+        ("d2q9_a8_random", m2r, 9, 8, (1, 1, 0), 0.7, (3e-6, 0, 0), 200, 0),
+        ("d2q9_a32_circles", m2, 9, 32, (0, 0, 0), 0.9, (1e-5, 0, 0), 150, 0),
+        ("d3q19_a4_spheres", m3, 19, 4, (1, 0, 0), 0.6, (1e-5, 0, 3e-6), 300, 0),
+        ("d3q19_a8_tubes", m3b, 19, 8, (1, 0, 0), 0.6, (1e-5, 0, 0), 200, 0),
+        ("d3q19_a4_incompressible", m3, 19, 4, (1, 0, 0), 0.7, (1e-5, 0, 0), 200, 1),
+        ("d2q9_a16_incompressible", m2, 9, 16, (1, 0, 0), 0.8, (1e-5, 0, 0), 200, 1),
+    ]
+
+
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("case", _small_cases(), ids=lambda c: c[0])
+def test_parity_small(oracle, case, arith):
+    name, mask, lattice, a, per, tau, F, steps, model = case
+    gpu, ref = run_both(oracle, mask, lattice, a, per, tau, F, steps, model, arith)
+    err = max_rel(gpu, ref, mask)
+    assert err <= TOL, (name, err)
+
+
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+def test_parity_d2q9_circles_128_full(oracle, arith):
+    """128^2 circles, 16^2 tiles, tau 0.8, F = 1e-6, 1000 steps, every node."""
+    mask, params, _ = geo.workload("d2q9_circles_128")
+    gpu, ref = run_both(oracle, mask, 9, 16, params["periodic"], params["tau"], params["force"],
+                        params["steps"], arith=arith)
+    assert max_rel(gpu, ref, mask) <= TOL
+
+
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+def test_parity_d3q19_spheres_64_2000_steps(oracle, arith):
+    """A 64^3 piece of the sphere-pack workload at its full step count."""
+    mask, _ = geo.sphere_pack_3d(64, seed=21)
+    gpu, ref = run_both(oracle, mask, 19, 4, (1, 0, 0), 0.6, (1e-6, 0, 0), 2000, arith=arith)
+    assert max_rel(gpu, ref, mask) <= TOL
+
+
+@pytest.mark.parametrize("name", ["d3q19_spheres_256", "d3q19_tubes_256"])
+def test_full_size_sampled_step_and_mass(oracle, name):
+    """Full 256^3 workloads in the benchmark's launch configuration: mass is
+    conserved over 2000 steps, and one further step matches the oracle's step
+    from the same state on sampled nodes (tile faces, edges, corners, walls)."""
+    _cuda()
+    mask, params, _ = geo.workload(name)
+    s = lbm.Solver(mask, 19, 4, params["periodic"], params["tau"], params["force"])
+    try:
+        st0, _ = s.stats()
+        s.step(params["steps"])
+        st1, rc = s.stats()
+        assert rc == 0 and st1.n_fluid == int(mask.sum())
+        assert abs(st1.mass - st0.mass) / st0.mass < 1e-12
+        f0 = s.export_pdfs()
+        s.step(1)
+        f1 = s.export_pdfs()
+    finally:
+        s.close()
+    flat = np.flatnonzero(mask.reshape(-1))
+    rng = np.random.default_rng(0)
+    pick = rng.choice(flat, 3000, replace=False)
+    # add nodes on tile boundaries in every direction
+    # plus nodes on the x faces of tiles (x % 4 in {0, 3}) spread over the box
+    edge = flat[(flat % 4 == 0) | (flat % 4 == 3)][::4001]
+    nodes = np.unique(np.concatenate([pick, edge]))
+    ref = oracle.step_nodes(19, mask, params["periodic"], params["tau"], params["force"], f0, nodes)
+    got = f1.reshape(19, -1)[:, nodes].T
+    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-13
+
+
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+def test_moments_and_stats(oracle, arith):
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(20, 17, 15), seed=5, r_min=2, r_max=4, target_fluid=0.5)
+    per, tau, F = (1, 0, 0), 0.65, (2e-5, -1e-5, 5e-6)
+    s = lbm.Solver(mask, 19, 4, per, tau, F, arith=arith)
+    try:
+        s.step(57)
+        rho, u, st, rc = s.moments()
+        f = s.export_pdfs()
+    finally:
+        s.close()
+    assert rc == 0
+    ref = oracle.run(19, mask, per, tau, F, oracle.init(19, mask), 57)
+    rrho, ru = oracle.moments(19, mask, per, F, ref)
+    fl = mask.astype(bool)
+    assert np.all(np.isnan(rho[~fl])) and np.all(np.isnan(u[:, ~fl]))
+    assert np.max(np.abs(rho[fl] - rrho[fl])) <= 1e-13
+    assert np.max(np.abs(u[:, fl] - ru[:, fl])) <= 1e-15
+    assert st.n_fluid == int(fl.sum())
+    assert st.mass == pytest.approx(float(np.sum(rrho[fl])), rel=1e-13)
+    assert st.mass == pytest.approx(oracle.total_mass(19, mask, f), rel=1e-13)
+    for k in range(3):
+        assert st.momentum[k] == pytest.approx(float(np.sum(rrho[fl] * ru[k][fl])), rel=1e-9, abs=1e-15)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(24, 16, 16), seed=8, r_min=2, r_max=4, target_fluid=0.5)
+    args = (mask, 19, 4, (1, 0, 0), 0.6, (1e-5, 0, 0))
+    a = lbm.Solver(*args)
+    a.step(100)
+    ck = a.export_pdfs()
+    a.step(50)
+    fa = a.export_pdfs()
+    a.close()
+    b = lbm.Solver(*args)
+    b.import_pdfs(ck, 100)
+    b.step(50)
+    fb = b.export_pdfs()
+    st, _ = b.stats()
+    b.close()
+    fl = mask.astype(bool)
+    assert np.array_equal(fa[:, fl].view(np.uint64), fb[:, fl].view(np.uint64))
+    assert st.step == 150
+
+
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+def test_edge_cases(oracle, arith):
+    _cuda()
+    # all solid: nothing to do, nothing to sum
+    s = lbm.Solver(np.zeros((8, 8, 8), np.uint8), 19, 4, arith=arith)
+    s.step(5)
+    st, rc = s.stats()
+    assert rc == 0 and st.n_fluid == 0 and st.mass == 0.0
+    s.close()
+    # a single fluid node surrounded by walls keeps its state
+    m = np.zeros((5, 6, 7), np.uint8)
+    m[2, 3, 4] = 1
+    gpu, ref = run_both(oracle, m, 19, 4, (0, 0, 0), 0.7, (1e-4, 0, 0), 10, arith=arith)
+    assert max_rel(gpu, ref, m) <= TOL
+    # one tile per periodic axis: every neighbour slot is the tile itself
+    m = np.ones((4, 4, 4), np.uint8)
+    gpu, ref = run_both(oracle, m, 19, 4, (1, 1, 1), 0.8, (1e-5, 2e-5, 0), 20, arith=arith)
+    assert max_rel(gpu, ref, m) <= TOL
+    m = np.ones((1, 16, 16), np.uint8)
+    m[0, 5, 5] = 0
+    gpu, ref = run_both(oracle, m, 9, 16, (1, 1, 0), 0.8, (1e-5, 0, 0), 20, arith=arith)
+    assert max_rel(gpu, ref, m) <= TOL
+
+
+def test_non_finite_state_is_reported():
+    """A NaN planted from the host is reported as LBM_ERR_DIVERGED, and the
+    context stays usable (no fault)."""
+    _cuda()
+    m = np.ones((8, 8, 8), np.uint8)
+    s = lbm.Solver(m, 19, 4, (1, 1, 1), 0.6, (1e-5, 0, 0))
+    f = s.export_pdfs()
+    f[3, 2, 2, 2] = np.nan
+    s.import_pdfs(f, 0)
+    s.step(3)
+    st, rc = s.stats()
+    assert rc == -5 and not np.isfinite(st.mass)
+    s.close()
+
+
+def test_residual_decreases_towards_steady_state():
+    _cuda()
+    m = geo.channel_2d(16, 16)
+    s = lbm.Solver(m, 9, 16, (1, 0, 0), 0.9, (1e-6, 0, 0))
+    st, _ = s.stats(residual=True)
+    assert st.residual == float("inf")
+    res = []
+    for _ in range(6):
+        s.step(200)
+        st, _ = s.stats(residual=True)
+        res.append(st.residual)
+    s.close()
+    assert all(b < a for a, b in zip(res, res[1:]))
