@@ -36,18 +36,22 @@ int lattice_q(int lattice);
 size_t bytes_per_value(int storage);
 
 // ---- kernel arguments --------------------------------------------------------
-// Constants of the fixed-point FP64 path (all values scaled by 2^60).
+// Constants of the fixed-point FP64 path (values scaled by 2^60 = "Q60"
+// unless stated; w = 1/tau, c = weight class, i = link).
 struct FixedConsts {
-    long long k_keep;       // (1 - omega) * 2^62: weight of the pre-collision value
-    long long k_rho[3];     // omega * w_c * 2^62 per weight class
-    long long k_j[3];       // 3 * omega * w_c * 2^62 per weight class
-    long long k_q[3];       // omega * w_c * 2^62 (scales the quadratic term)
-    long long half_f[3];    // F/2 in units of 2^-60
-    long long s_odd[19];    // (1 - omega/2) w_i 3 c_i.F in units of 2^-60
-    long long k_force;      // (1 - omega/2) * 2^62
-    long long f_sc[3];      // F * 2^60 for the quadratic forcing part
-    long long w_bits[3];    // bit patterns of the weights w_c (FP64)
-    long long wsum_fix;     // sum_i w_i (exact) in units of 2^-60
+    long long w_bits[3];  // FP64 bit patterns of the class weights w_c
+    long long w60[3];     // w_c in Q60 (exact)
+    long long kw[3];      // w_c * 2^62
+    long long k_keep;     // (1 - w) * 2^62
+    long long k_rho[3];   // w * w_c * 2^62
+    long long k_j[3];     // 3 w w_c * 2^61
+    long long alpha;      // 4.5 w * 2^59
+    long long g1;         // 1.5 w * 2^61
+    long long kf[3];      // 3 (1 - w/2) F_a in Q60
+    long long half_f[3];  // F_a / 2 in Q60
+    long long beta[19];   // 9 (1 - w/2) (c_i.F) in Q60
+    long long so[19];     // 3 (1 - w/2) w_i (c_i.F) in Q60
+    long long dws;        // sum_i w_i in Q60, minus 2^60 (exact)
 };
 
 struct StepArgs {
