@@ -196,6 +196,38 @@ int lbm_export_pdfs(lbm_ctx* ctx, double* pdfs, int flags, void* stream);
 int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
                     void* stream);
 
+/* Largest number of partial-sum blocks lbm_stats_noalloc can hold: its
+ * static scratch is LBM_NOALLOC_MAX_BLOCKS * 8 doubles (4 MiB) per GPU. */
+#define LBM_NOALLOC_MAX_BLOCKS 65536
+
+/* The mass and momentum sums of lbm_moments without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they want the sums -- code working inside a
+ * fixed device-memory budget owned by another allocator, monitoring hooks
+ * that must not change the memory footprint between steps, or loops that
+ * cannot afford the device-wide synchronisation cudaMalloc implies.
+ *   ctx        a context from lbm_init (its tables were allocated there).
+ *   stats_dev  device, caller-allocated, 8 doubles: on completion
+ *              [mass, momentum x, y, z, sum |u|^2, 0, fluid-node count, 0]
+ *              with the meanings of lbm_stats; no residual.
+ *   stream     cudaStream_t; the call only enqueues work (nothing is copied
+ *              to the host and the stream is not synchronised).
+ * The per-block partial sums go to a file-scope device array of
+ * LBM_NOALLOC_MAX_BLOCKS * 8 doubles that every GPU loading the library
+ * keeps until the process exits.  One partial block covers 4 non-empty
+ * tiles of 4^3 or 8^2 nodes, or one tile of 8^3, 16^2 or 32^2 nodes, so
+ * tilings that need more than LBM_NOALLOC_MAX_BLOCKS blocks (more than
+ * 262,144 non-empty 4^3 tiles, for example) are rejected with
+ * LBM_ERR_CAPACITY.  The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array, which keeps the last call's contents: every
+ * block writes its slots before they are read, so nothing has to start at
+ * zero, but calls whose kernels overlap on the GPU race with each other.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
+int lbm_stats_noalloc(const lbm_ctx* ctx, double* stats_dev, void* stream);
+
 /* Counts of the context's tiling (see lbm_tiling).  Errors: LBM_ERR_ARG. */
 int lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out);
 

@@ -382,3 +382,19 @@ extern "C" int lbm_free(lbm_ctx* c) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize in lbm_free");
     return LBM_OK;
 }
+
+namespace lbm {
+// Reduction launch data of a context, for entry points defined in other files.
+int ctx_reduction_args(const lbm_ctx* c, NodeArgs* args, NodeLaunch* moments, int* nblocks) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+    *args = c->na;
+    args->pdf = c->pdf[c->cur];
+    args->rho_out = nullptr;
+    args->u_out = nullptr;
+    args->residual = 0;
+    args->u_saved = nullptr;
+    *moments = c->moments_fn;
+    *nblocks = c->nblocks;
+    return LBM_OK;
+}
+}  // namespace lbm

@@ -25,7 +25,8 @@ LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED = 0, 1, 2
 LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
 
 EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
-            "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error")
+            "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc")
+LBM_NOALLOC_MAX_BLOCKS = 65536
 
 
 class LBMError(RuntimeError):
@@ -78,6 +79,7 @@ def library(build: bool = True):
             lib.lbm_import_pdfs.argtypes = [P, P, ctypes.c_int64, I, P]
             lib.lbm_get_tiling.argtypes = [P, ctypes.POINTER(lbm_tiling)]
             lib.lbm_free.argtypes = [P]
+            lib.lbm_stats_noalloc.argtypes = [P, P, P]
             lib.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
                 getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -171,6 +173,12 @@ def lbm_get_tiling(ctx) -> lbm_tiling:
     info = lbm_tiling()
     _check(library().lbm_get_tiling(ctx, ctypes.byref(info)))
     return info
+
+
+def lbm_stats_noalloc(ctx, stats_dev, stream=None):
+    """Mass/momentum sums into a caller-allocated device buffer of 8 doubles,
+    without any device allocation (see include/lbm.h)."""
+    return _check(library().lbm_stats_noalloc(ctx, _ptr(stats_dev), stream))
 
 
 def lbm_free(ctx):
