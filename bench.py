@@ -47,8 +47,12 @@ def parse():
     ap.add_argument("--workload", default="d3q19_spheres_256")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--arith", default="auto", choices=["auto", "f64", "fixed"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32", "f32s", "f16s"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "steady"])
+    ap.add_argument("--max-steps", type=int, default=100000)
+    ap.add_argument("--target", type=float, default=1e-6)
     return ap.parse_args()
 
 
@@ -202,8 +206,10 @@ def run_ours(args):
     mask, params, info = geo.workload(args.workload)
     lat, a = params["lattice"], params["tile_a"]
     arith = {"auto": lbm.LBM_ARITH_AUTO, "f64": lbm.LBM_ARITH_F64, "fixed": lbm.LBM_ARITH_FIXED}[args.arith]
+    storage = {"f64": lbm.LBM_STORE_F64, "f32": lbm.LBM_STORE_F32, "f32s": lbm.LBM_STORE_F32S,
+               "f16s": lbm.LBM_STORE_F16S}[args.storage]
     solver = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], arith=arith,
-                        device=dev)
+                        storage=storage, device=dev)
     stream = solver.stream
     n_fluid = int(solver.tiling.n_fluid)
 
@@ -256,12 +262,13 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(mask, params, args.steps, arith, dev, world)
+        e2e = run_e2e(mask, params, args.steps, arith, dev, world, storage)
 
     if rank != 0:
         return
     peaks, peak_kind = load_peaks()
-    bytes_per_launch = n_fluid * B_NODE[lat]
+    s_d = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2}[args.storage]
+    bytes_per_launch = n_fluid * pm.B_node(lat, s_d)
     achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
     traffic, tnote = committed_traffic(args.workload, arith_name)
     tiling_stats = {"n_ftiles": int(tiling.n_ftiles), "n_tiles": int(tiling.n_tiles),
@@ -271,10 +278,12 @@ def run_ours(args):
         "metric": "D3Q19 sparse MLUPS + % HBM roofline" if lat == 19 else "D2Q9 sparse MLUPS + % HBM roofline",
         "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "f32s": "f32", "f16s": "f16+f32"}[args.storage],
+        "data": "synthetic",
         "config": {"workload": args.workload, "lattice": f"D{3 if lat == 19 else 2}Q{lat}",
                    "size": list(mask.shape[::-1]), "tile": a, "fluid_nodes": n_fluid, **tiling_stats,
-                   "tau": params["tau"], "force": params["force"], "storage": "f64", "arith": arith_name,
+                   "tau": params["tau"], "force": params["force"], "storage": args.storage,
+                   "arith": arith_name if args.storage == "f64" else "f32",
                    "stats_every": STATS_EVERY, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (two PDF copies of "
                          f"{tiling.pdf_bytes / 1e9:.2f} GB each, L2 129 MB)",
@@ -296,7 +305,7 @@ def run_ours(args):
     print(json.dumps(line))
 
 
-def run_e2e(mask, params, steps, arith, dev, world):
+def run_e2e(mask, params, steps, arith, dev, world, storage=0):
     """Same metric through the C ABI from host buffers: pinned host mask ->
     lbm_init (tiling + upload + equilibrium fill), the timed steps with the
     stats read back every 100 steps, and rho/u fields back to host memory."""
@@ -305,7 +314,8 @@ def run_e2e(mask, params, steps, arith, dev, world):
     from paper_1703_08015_gb300 import lbm
 
     lat, a = params["lattice"], params["tile_a"]
-    p = lbm.make_params(lat, mask.shape, a, params["periodic"], params["tau"], params["force"], arith=arith)
+    p = lbm.make_params(lat, mask.shape, a, params["periodic"], params["tau"], params["force"], arith=arith,
+                        storage=storage)
     info, _, _ = lbm.lbm_build_tilemap(p, mask, want_map=False, want_nbr=False)
     nbytes = max(int(info.pdf_bytes), 256)
     bufs = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
@@ -345,10 +355,75 @@ def ctypes_stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def run_steady(args):
+    """Time to steady state (residual below --target, checked every 100 steps
+    with the FP64 reduction) for the FP64 path and the FP32 / FP16 storage
+    forms, from rest, on one GPU; errors of the reduced forms against FP64."""
+    import torch
+
+    from paper_1703_08015_gb300 import lbm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mask, params, info = geo.workload(args.workload)
+    lat, a = params["lattice"], params["tile_a"]
+    nu = (params["tau"] - 0.5) / 3.0
+    fx = params["force"][0]
+    forms = [("f64", lbm.LBM_STORE_F64), ("f32", lbm.LBM_STORE_F32), ("f32s", lbm.LBM_STORE_F32S),
+             ("f16s", lbm.LBM_STORE_F16S)]
+    res = {}
+    fields = {}
+    for name, storage in forms:
+        s = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], storage=storage,
+                       device=dev)
+        st0, _ = s.stats(residual=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        n, st, hist = 0, st0, []
+        while n < args.max_steps:
+            s.step(STATS_EVERY)
+            n += STATS_EVERY
+            st, rc = s.stats(residual=True)
+            hist.append(st.residual)
+            if rc != 0 or st.residual < args.target:
+                break
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        rho, u, st_f, _ = s.moments()
+        s.close()
+        fl = mask.astype(bool)
+        k = nu * float(np.sum(u[0][fl])) / mask.size / fx if fx else None  # superficial-velocity permeability
+        fields[name] = u[:, fl]
+        res[name] = {"steps": n, "seconds": dt, "converged": bool(st.residual < args.target),
+                     "final_residual": st.residual, "mlups": int(st.n_fluid) * n / dt / 1e6,
+                     "permeability": k, "mass_drift": abs(st.mass - st0.mass) / st0.mass,
+                     "residual_floor": float(min(hist)) if hist else None}
+    ref = fields["f64"]
+    for name in ("f32", "f32s", "f16s"):
+        d = fields[name] - ref
+        res[name]["velocity_l2_rel_err_vs_f64"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+        if res["f64"]["permeability"]:
+            res[name]["permeability_rel_err_vs_f64"] = abs(res[name]["permeability"] / res["f64"]["permeability"] - 1)
+        res[name]["speedup_vs_f64"] = res["f64"]["seconds"] / res[name]["seconds"]
+    if rank == 0:
+        print(json.dumps({"metric": "time to steady state (residual < %g) vs plain FP64" % args.target,
+                          "value": res["f64"]["seconds"] / min(r["seconds"] for k, r in res.items()
+                                                               if k != "f64" and r["converged"])
+                          if any(r["converged"] for k, r in res.items() if k != "f64") else None,
+                          "unit": "x speedup of the fastest reduced form", "higher_is_better": True,
+                          "n_gpus": 1, "data": "synthetic",
+                          "config": {"workload": args.workload, "check_every": STATS_EVERY,
+                                     "max_steps": args.max_steps, "geometry": info},
+                          "forms": res}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "steady":
+        run_steady(args)
     else:
         run_ours(args)
 

@@ -70,6 +70,7 @@ extern "C" {
 #define LBM_STORE_F64  0
 #define LBM_STORE_F32  1 /* FP32 values, FP32 collision (not in the paper) */
 #define LBM_STORE_F16S 2 /* FP16 scaled deviations (f_i - w_i) * S, FP32 collision (not in the paper) */
+#define LBM_STORE_F32S 3 /* FP32 deviations f_i - w_i, FP32 collision (not in the paper) */
 
 /* Arithmetic of the FP64 step.  Both variants compute the same update; they
  * differ only in rounding (see lbm_step). */
@@ -96,7 +97,8 @@ typedef struct lbm_params {
     double rho0;      /* density of the rest start (used when no rho field is given) */
     int storage;      /* LBM_STORE_* */
     int arith;        /* LBM_ARITH_* (LBM_STORE_F64 only) */
-    double f16_scale; /* LBM_STORE_F16S: scale S of the deviations; 0 = default 2^14 */
+    double f16_scale; /* LBM_STORE_F16S: scale S of the deviations (a power of two
+                         keeps the scaling exact); 0 = default 2^16 */
 } lbm_params;
 
 typedef struct lbm_tiling {

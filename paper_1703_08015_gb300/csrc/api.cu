@@ -35,6 +35,10 @@ struct lbm_ctx {
     int32_t* d_nbr = nullptr;
     uint64_t* d_tmask = nullptr;
     int32_t* d_coords = nullptr;
+    uint32_t* d_nodes = nullptr;
+    WorkBlock* d_blocks = nullptr;
+    long long* d_tile_off = nullptr;
+    int32_t* d_tile_stride = nullptr;
     double* d_partials = nullptr;
     double* d_result = nullptr;
     double* d_u_saved = nullptr;
@@ -93,6 +97,10 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_nbr);
     cudaFree(c->d_tmask);
     cudaFree(c->d_coords);
+    cudaFree(c->d_nodes);
+    cudaFree(c->d_blocks);
+    cudaFree(c->d_tile_off);
+    cudaFree(c->d_tile_stride);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_u_saved);
@@ -138,7 +146,7 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(LBM_ERR_OOM, "host allocation failed");
     c->p = *p;
-    if (c->p.storage == LBM_STORE_F16S && !(c->p.f16_scale > 0.0)) c->p.f16_scale = 16384.0;
+    if (c->p.storage == LBM_STORE_F16S && !(c->p.f16_scale > 0.0)) c->p.f16_scale = 65536.0;
     c->info = T.info;
     c->q = lattice_q(p->lattice);
     c->nt = T.a * T.a * (T.d == 3 ? T.a : 1);
@@ -178,6 +186,11 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     TRY(upload(&c->d_nbr, T.nbr, s));
     TRY(upload(&c->d_tmask, T.tmask, s));
     TRY(upload(&c->d_coords, T.coords, s));
+    build_work_list(&T, work_threads_for(p->lattice, p->tile_a), 16);
+    TRY(upload(&c->d_nodes, T.nodes, s));
+    TRY(upload(&c->d_blocks, T.blocks, s));
+    TRY(upload(&c->d_tile_off, T.tile_off, s));
+    TRY(upload(&c->d_tile_stride, T.tile_stride, s));
     CTRY(cudaMalloc(&c->d_partials, (size_t)(c->nblocks > 0 ? c->nblocks : 1) * 8 * sizeof(double)));
     CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double)));
     CTRY(cudaMalloc(&c->d_err, sizeof(int)));
@@ -185,8 +198,13 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     CTRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
 
     StepArgs& sa = c->sa;
+    sa.blocks = c->d_blocks;
+    sa.nodes = c->d_nodes;
+    sa.n_work_blocks = (int)T.blocks.size();
     sa.nbr = c->d_nbr;
     sa.tmask = c->d_tmask;
+    sa.tile_off = c->d_tile_off;
+    sa.tile_stride = c->d_tile_stride;
     sa.n_tiles = nf;
     sa.tau = p->tau;
     sa.omega = 1.0 / p->tau;
@@ -204,6 +222,8 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     na.nbr = c->d_nbr;
     na.tmask = c->d_tmask;
     na.coords = c->d_coords;
+    na.tile_off = c->d_tile_off;
+    na.tile_stride = c->d_tile_stride;
     na.n_tiles = nf;
     na.nx = p->nx;
     na.ny = p->ny;

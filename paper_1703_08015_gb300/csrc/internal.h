@@ -21,6 +21,13 @@ int cuda_fail(cudaError_t e, const char* what);    // LBM_ERR_CUDA or LBM_ERR_OO
         if (e_ != cudaSuccess) return ::lbm::cuda_fail(e_, #call); \
     } while (0)
 
+// A block of the step kernels: `count` consecutive entries of the fluid-node
+// list starting at `node_begin`, drawn from the `n_tiles` consecutive
+// non-empty tiles starting at `tile_begin`.
+struct WorkBlock {
+    int node_begin, count, tile_begin, n_tiles;
+};
+
 // ---- host tiling ------------------------------------------------------------
 struct HostTiling {
     lbm_tiling info{};
@@ -29,9 +36,17 @@ struct HostTiling {
     std::vector<int32_t> nbr;                // [n_ftiles][nn]
     std::vector<uint64_t> tmask;             // [n_ftiles][words], bit n = node n fluid
     std::vector<int32_t> coords;             // [n_ftiles][3] tile coordinates
+    std::vector<long long> tile_off;         // [n_ftiles] first value of the tile's PDF block
+    std::vector<int32_t> tile_stride;        // [n_ftiles] values per link (fluid count, sector-padded)
+    std::vector<uint32_t> nodes;             // fluid nodes, tile-major: tile * NT + node
+    std::vector<WorkBlock> blocks;           // step-kernel blocks over `nodes`
 };
 int validate_params(const lbm_params* p);
 int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out);
+// Fluid-node list and step-kernel blocks of at most `threads` nodes and
+// `max_tiles` tiles each.
+void build_work_list(HostTiling* T, int threads, int max_tiles);
+int work_threads_for(int lattice, int a);
 int lattice_q(int lattice);
 size_t bytes_per_value(int storage);
 
@@ -55,10 +70,15 @@ struct FixedConsts {
 };
 
 struct StepArgs {
+    const WorkBlock* blocks;  // [n_work_blocks]
+    const uint32_t* nodes;    // fluid-node list: tile * NT + node
+    int n_work_blocks;
     const void* src;
     void* dst;
     const int32_t* nbr;
     const uint64_t* tmask;
+    const long long* tile_off;  // compact layout: PDF block of each tile (in values)
+    const int32_t* tile_stride; // compact layout: values per link of each tile
     int n_tiles;
     double omega;         // 1 / tau
     double tau;
@@ -76,6 +96,8 @@ struct NodeArgs {         // kernels that visit every node of every tile
     const int32_t* nbr;
     const uint64_t* tmask;
     const int32_t* coords;
+    const long long* tile_off;
+    const int32_t* tile_stride;
     int n_tiles;
     int nx, ny, nz;
     double force[3];

@@ -34,12 +34,11 @@ __global__ void k_init(const NodeArgs a) {
     const int node = threadIdx.x;
     if (tile >= a.n_tiles) return;
     const NodePos<A> p = node_pos<TL>(node);
-    T* out = static_cast<T*>(const_cast<void*>(a.pdf)) + (size_t)tile * L::Q * TL::NT + node;
     size_t n = 0;
-    if (!own_fluid<TL>(a.tmask, tile, node) || !dense_index<L, A>(a, tile, p, n)) {
-        static_for<0, L::Q>([&](auto I) { out[decltype(I)::value * TL::NT] = (T)0; });
-        return;
-    }
+    if (!own_fluid<TL>(a.tmask, tile, node) || !dense_index<L, A>(a, tile, p, n)) return;
+    const int stride = a.tile_stride[tile];
+    T* out = static_cast<T*>(const_cast<void*>(a.pdf)) + a.tile_off[tile] +
+             fluid_rank<TL::W>(a.tmask + (size_t)tile * TL::W, node);
     const double rho = a.rho_in ? a.rho_in[n] : a.rho0;
     const size_t N = (size_t)a.nx * a.ny * a.nz;
     const double ux = a.u_in ? a.u_in[n] : 0.0;
@@ -52,7 +51,7 @@ __global__ void k_init(const NodeArgs a) {
         const double cu = K::cx * ux + K::cy * uy + K::cz * uz;
         const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
         const double feq = MODEL == LBM_QUASI_COMPRESSIBLE ? K::w * rho * (1.0 + poly) : K::w * (rho + poly);
-        out[i * TL::NT] = S::template from_f64<L, i>(feq, a.f16_scale);
+        out[i * stride] = S::template from_f64<L, i>(feq, a.f16_scale);
     });
 }
 
@@ -62,14 +61,14 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
     using TL = Tile<L, A>;
     using T = typename S::T;
     constexpr int NTH = TPB * TL::NT;
-    constexpr size_t TILE_BYTES = sizeof(T) * L::Q * TL::NT;
     __shared__ NeighShared<TL, TPB> sh;
     __shared__ double red[NTH / 32][kStats];
     const int lt = threadIdx.x / TL::NT;
     const int node = threadIdx.x - lt * TL::NT;
     const int tile = blockIdx.x * TPB + lt;
-    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, static_cast<const unsigned char*>(a.pdf), TILE_BYTES,
-                                 a.n_tiles, tile, lt, node);
+    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, a.tile_off, a.tile_stride,
+                                 static_cast<const unsigned char*>(a.pdf), (int)sizeof(T), a.n_tiles, tile, lt,
+                                 node);
     __syncthreads();
     double acc[kStats];
 #pragma unroll
@@ -159,10 +158,12 @@ __global__ void k_export(const NodeArgs a) {
     size_t n;
     if (!dense_index<L, A>(a, tile, p, n)) return;
     const size_t N = (size_t)a.nx * a.ny * a.nz;
-    const T* in = static_cast<const T*>(a.pdf) + (size_t)tile * L::Q * TL::NT + node;
+    const int stride = a.tile_stride[tile];
+    const T* in = static_cast<const T*>(a.pdf) + a.tile_off[tile] +
+                  fluid_rank<TL::W>(a.tmask + (size_t)tile * TL::W, node);
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        a.dense_pdf[i * N + n] = S::template to_f64<L, i>(in[i * TL::NT], a.f16_inv_scale);
+        a.dense_pdf[i * N + n] = S::template to_f64<L, i>(in[i * stride], a.f16_inv_scale);
     });
 }
 
@@ -176,10 +177,12 @@ __global__ void k_import(const NodeArgs a) {
     size_t n;
     if (!dense_index<L, A>(a, tile, p, n)) return;
     const size_t N = (size_t)a.nx * a.ny * a.nz;
-    T* out = static_cast<T*>(const_cast<void*>(a.pdf)) + (size_t)tile * L::Q * TL::NT + node;
+    const int stride = a.tile_stride[tile];
+    T* out = static_cast<T*>(const_cast<void*>(a.pdf)) + a.tile_off[tile] +
+             fluid_rank<TL::W>(a.tmask + (size_t)tile * TL::W, node);
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        out[i * TL::NT] = S::template from_f64<L, i>(a.dense_pdf_in[i * N + n], a.f16_scale);
+        out[i * stride] = S::template from_f64<L, i>(a.dense_pdf_in[i * N + n], a.f16_scale);
     });
 }
 
@@ -255,6 +258,7 @@ int node_blocks(int lattice, int a, int n_tiles) {
         case LBM_STORE_F64: return &F<__VA_ARGS__, StoreF64>;      \
         case LBM_STORE_F32: return &F<__VA_ARGS__, StoreF32>;      \
         case LBM_STORE_F16S: return &F<__VA_ARGS__, StoreF16S>;    \
+        case LBM_STORE_F32S: return &F<__VA_ARGS__, StoreF32S>;    \
         default: return nullptr;                                   \
     }
 

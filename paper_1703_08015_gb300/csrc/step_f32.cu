@@ -1,8 +1,154 @@
-// step_f32.cu -- reduced-precision storage forms (FP32, FP16 deviations).
+// step_f32.cu -- reduced-precision storage forms of the tiled step (not in
+// the paper): PDFs stored as FP32 values, as FP32 deviations f_i - w_i, or as
+// FP16 deviations h_i = RN_fp16((f_i - w_i) * S) with a power-of-two scale S;
+// the collision runs in FP32 in every case.  Storing deviations keeps the
+// rounding relative to f_i - w_i, so slow hydrodynamic drifts are not lost
+// in the rounding of f_i ~ w_i.
+//
+// The collision works on deviations g_i = f_i - w_i so that FP32 rounding acts
+// on the small deviation, not on f_i itself:
+//   rho - 1 = sum g_i,   j = sum c_i g_i + F/2,   u = j / rho  (Eq. 5; Eq. 6: u = j)
+//   f^eq_i - w_i = w_i [ (rho - 1) + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u) ]   (Eq. 3)
+//                = w_i [ (rho - 1) + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u ]          (Eq. 4)
+//   g*_i = g_i - (g_i - (f^eq_i - w_i)) / tau + S_i  (Eq. 7 with Eq. 2, Guo forcing S_i)
 #include "tile.cuh"
 
 namespace lbm {
 
-StepLaunch select_step_f32(int, int, int, int) { return nullptr; }
+template <class L, class S>
+struct F32Io;
+
+template <class L>
+struct F32Io<L, StoreF32> {
+    template <int I>
+    __device__ static __forceinline__ float dev(unsigned int r, const StepArgs&) {
+        return __uint_as_float(r) - (float)Link<L, I>::w;
+    }
+    template <int I>
+    __device__ static __forceinline__ unsigned int raw(float g, const StepArgs&) {
+        return __float_as_uint((float)Link<L, I>::w + g);
+    }
+};
+
+template <class L>
+struct F32Io<L, StoreF32S> {
+    template <int I>
+    __device__ static __forceinline__ float dev(unsigned int r, const StepArgs&) {
+        return __uint_as_float(r);
+    }
+    template <int I>
+    __device__ static __forceinline__ unsigned int raw(float g, const StepArgs&) {
+        return __float_as_uint(g);
+    }
+};
+
+template <class L>
+struct F32Io<L, StoreF16S> {
+    template <int I>
+    __device__ static __forceinline__ float dev(unsigned short r, const StepArgs& a) {
+        return __half2float(__ushort_as_half(r)) * a.f16_inv_scale_f;
+    }
+    template <int I>
+    __device__ static __forceinline__ unsigned short raw(float g, const StepArgs& a) {
+        return __half_as_ushort(__float2half_rn(g * a.f16_scale_f));
+    }
+};
+
+template <class L, int MODEL>
+__device__ __forceinline__ void collide_f32(float (&g)[L::Q], float omega, const float* F) {
+    float dr = 0.f, jx = 0.5f * F[0], jy = 0.5f * F[1], jz = 0.5f * F[2];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using K = Link<L, i>;
+        dr += g[i];
+        if constexpr (K::cx > 0) jx += g[i];
+        if constexpr (K::cx < 0) jx -= g[i];
+        if constexpr (K::cy > 0) jy += g[i];
+        if constexpr (K::cy < 0) jy -= g[i];
+        if constexpr (K::cz > 0) jz += g[i];
+        if constexpr (K::cz < 0) jz -= g[i];
+    });
+    const float rho = 1.f + dr;
+    float ux = jx, uy = jy, uz = jz;
+    if constexpr (MODEL == LBM_QUASI_COMPRESSIBLE) {
+        const float inv = 1.f / rho;
+        ux *= inv;
+        uy *= inv;
+        uz *= inv;
+    }
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float uF = ux * F[0] + uy * F[1] + uz * F[2];
+    const float kf = 1.f - 0.5f * omega;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using K = Link<L, i>;
+        constexpr float w = (float)K::w;
+        const float cu = K::cx * ux + K::cy * uy + K::cz * uz;
+        const float cF = K::cx * F[0] + K::cy * F[1] + K::cz * F[2];
+        const float poly = 3.f * cu + 4.5f * cu * cu - 1.5f * usq;
+        const float geq = w * (dr + (MODEL == LBM_QUASI_COMPRESSIBLE ? rho * poly : poly));
+        const float Sf = kf * w * (3.f * (cF - uF) + 9.f * cu * cF);
+        g[i] = g[i] - omega * (g[i] - geq) + Sf;
+    });
+}
+
+template <class L, int A, int MODEL, class S>
+__global__ void __launch_bounds__(work_threads<L, A>()) k_step_f32(const StepArgs a) {
+    using TL = Tile<L, A>;
+    using T = typename S::T;
+    using IO = F32Io<L, S>;
+    __shared__ NeighShared<TL, work_tiles()> sh;
+    WorkNode wn;
+    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    const NodePos<A> p = node_pos<TL>(wn.node);
+    T raw[L::Q];
+    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
+    const int stride = sh.stride[wn.lt][TL::CENTER];
+    float g[L::Q];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        g[i] = IO::template dev<i>(raw[i], a);
+    });
+    collide_f32<L, MODEL>(g, a.omega_f, a.force_f);
+    T* out = static_cast<T*>(a.dst) +
+             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        out[i * stride] = IO::template raw<i>(g[i], a);
+    });
+}
+
+template <class L, int A, int MODEL, class S>
+cudaError_t launch_step_f32(const StepArgs& a, cudaStream_t s) {
+    if (a.n_work_blocks == 0) return cudaSuccess;
+    k_step_f32<L, A, MODEL, S><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class L, int A, class S>
+static StepLaunch pick(int model) {
+    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_f32<L, A, LBM_QUASI_COMPRESSIBLE, S>
+                                           : &launch_step_f32<L, A, LBM_INCOMPRESSIBLE, S>;
+}
+
+template <class L, int A>
+static StepLaunch pick_storage(int model, int storage) {
+    if (storage == LBM_STORE_F32) return pick<L, A, StoreF32>(model);
+    if (storage == LBM_STORE_F16S) return pick<L, A, StoreF16S>(model);
+    if (storage == LBM_STORE_F32S) return pick<L, A, StoreF32S>(model);
+    return nullptr;
+}
+
+StepLaunch select_step_f32(int lattice, int a, int model, int storage) {
+    if (lattice == LBM_D2Q9) {
+        if (a == 8) return pick_storage<D2Q9, 8>(model, storage);
+        if (a == 16) return pick_storage<D2Q9, 16>(model, storage);
+        if (a == 32) return pick_storage<D2Q9, 32>(model, storage);
+    } else if (lattice == LBM_D3Q19) {
+        if (a == 4) return pick_storage<D3Q19, 4>(model, storage);
+        if (a == 8) return pick_storage<D3Q19, 8>(model, storage);
+    }
+    return nullptr;
+}
 
 }  // namespace lbm

@@ -1,47 +1,40 @@
-// step_f64.cu -- the tiled step (Fig. 5) with native FP64 arithmetic, for
-// every storage format: raw words are gathered, widened to FP64, collided,
-// narrowed and stored back into the node's own slots of the other copy.
+// step_f64.cu -- the tiled step (Fig. 5) with native FP64 arithmetic: raw
+// words are gathered, widened to FP64, collided, and stored into the node's
+// own slots of the other copy.  One thread per fluid node (work list).
 #include "collide_f64.cuh"
 #include "tile.cuh"
 
 namespace lbm {
 
-template <class L, int A, int TPB, int MODEL, class S>
-__global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_step_f64(const StepArgs a) {
+template <class L, int A, int MODEL, class S>
+__global__ void __launch_bounds__(work_threads<L, A>()) k_step_f64(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
-    constexpr size_t TILE_BYTES = sizeof(T) * L::Q * TL::NT;
-    __shared__ NeighShared<TL, TPB> sh;
-    const int lt = threadIdx.x / TL::NT;
-    const int node = threadIdx.x - lt * TL::NT;
-    const int tile = blockIdx.x * TPB + lt;
-    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, static_cast<const unsigned char*>(a.src), TILE_BYTES,
-                                 a.n_tiles, tile, lt, node);
-    __syncthreads();  // the only barrier (Fig. 5, step 4)
-    if (tile >= a.n_tiles || !mask_bit(sh, lt, TL::CENTER, node)) return;
-
-    const NodePos<A> p = node_pos<TL>(node);
+    __shared__ NeighShared<TL, work_tiles()> sh;
+    WorkNode wn;
+    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    const NodePos<A> p = node_pos<TL>(wn.node);
     T raw[L::Q];
-    gather<L, A, TPB, T>(sh, lt, node, p, raw);
+    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
+    const int stride = sh.stride[wn.lt][TL::CENTER];
     double f[L::Q];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         f[i] = S::template to_f64<L, i>(raw[i], a.f16_inv_scale);
     });
     collide_f64<L, MODEL>(f, a.omega, a.force);
-    T* out = static_cast<T*>(a.dst) + (size_t)tile * L::Q * TL::NT + node;
+    T* out = static_cast<T*>(a.dst) +
+             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        out[i * TL::NT] = S::template from_f64<L, i>(f[i], a.f16_scale);
+        out[i * stride] = S::template from_f64<L, i>(f[i], a.f16_scale);
     });
 }
 
 template <class L, int A, int MODEL, class S>
 cudaError_t launch_step_f64(const StepArgs& a, cudaStream_t s) {
-    constexpr int TPB = tiles_per_block<L, A>();
-    const int blocks = (a.n_tiles + TPB - 1) / TPB;
-    if (blocks == 0) return cudaSuccess;
-    k_step_f64<L, A, TPB, MODEL, S><<<blocks, TPB * Tile<L, A>::NT, 0, s>>>(a);
+    if (a.n_work_blocks == 0) return cudaSuccess;
+    k_step_f64<L, A, MODEL, S><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@
 // recomputed with native FP64 instructions, so every node gets the FP64
 // update; only the rounding differs between the two paths.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "collide_f64.cuh"
@@ -78,17 +79,28 @@ __device__ __forceinline__ bool small(long long x, int log2bound) {
     return (unsigned long long)(x + (1ll << log2bound)) < (2ull << log2bound);
 }
 
+template <class L, int C>
+constexpr int first_of_class() {
+    int i = 0;
+    while (i < L::Q && L::cls_[i] != C) i++;
+    return i;
+}
+
+// The fixed-point update of one node.  `out` points at the node's slot of
+// link 0 in the destination tile (links are `stride` apart); each +-c pair is
+// stored as soon as it is computed.  Returns false when the node must be
+// recomputed in FP64 (its stores are then overwritten by the caller).
 template <class L, int MODEL>
-__device__ __forceinline__ bool collide_fixed(unsigned long long (&b)[L::Q], const FixedConsts& k) {
+__device__ __forceinline__ bool collide_fixed(const unsigned long long (&b)[L::Q], const FixedConsts& k,
+                                              unsigned long long* out, int stride) {
     constexpr int Q = L::Q;
     long long g[Q];
     bool ok = true;
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        using F = FixLink<L, i>;
         const unsigned long long wb = (unsigned long long)k.w_bits[Link<L, i>::cls];
         ok &= ((b[i] ^ wb) >> 52) == 0;
-        g[i] = (long long)(b[i] - wb) << F::SHIFT;
+        g[i] = (long long)(b[i] - wb) << FixLink<L, i>::SHIFT;
     });
     long long dr = k.dws, jx = k.half_f[0], jy = k.half_f[1], jz = k.half_f[2];
     static_for<0, Q>([&](auto I) {
@@ -106,92 +118,91 @@ __device__ __forceinline__ bool collide_fixed(unsigned long long (&b)[L::Q], con
     if (!ok) return false;
 
     // 1 / rho = 1 + e: start from 1 - d + d^2, two Newton steps (error < 2^-60 for |d| < 2^-5)
-    long long e = -dr + qmul<60>(dr, dr);
+    long long e = 0;
+    if constexpr (MODEL == LBM_QUASI_COMPRESSIBLE) {
+        e = -dr + qmul<60>(dr, dr);
 #pragma unroll
-    for (int it = 0; it < 2; it++) {
-        const long long t = dr + e + qmul<60>(dr, e);  // rho (1 + e) - 1
-        e = e - t - qmul<60>(e, t);
+        for (int it = 0; it < 2; it++) {
+            const long long t = dr + e + qmul<60>(dr, e);  // rho (1 + e) - 1
+            e = e - t - qmul<60>(e, t);
+        }
     }
-    long long V[3];  // w_c / rho (quasi-compressible) or w_c (incompressible)
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-        V[c] = MODEL == LBM_QUASI_COMPRESSIBLE ? k.w60[c] + qmul<62>(e, k.kw[c]) : k.w60[c];
-    const long long jj = qmul<60>(jx, jx) + qmul<60>(jy, jy) + qmul<60>(jz, jz);
+    const long long jj = qmul<60>(jx, jx) + qmul<60>(jy, jy) + (L::D == 3 ? qmul<60>(jz, jz) : 0);
     const long long gamma = qmul<61>(jj, k.g1) + qmul<60>(jx, k.kf[0]) + qmul<60>(jy, k.kf[1]) +
-                            qmul<60>(jz, k.kf[2]);
-    long long R[3], PX[3], PY[3], PZ[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        R[c] = qmul<62>(dr, k.k_rho[c]);
-        PX[c] = qmul<61>(jx, k.k_j[c]);
-        PY[c] = qmul<61>(jy, k.k_j[c]);
-        PZ[c] = L::D == 3 ? qmul<61>(jz, k.k_j[c]) : 0;
-    }
-    long long E[Q];  // even (pair) part, valid at representative links
-    long long O[Q];  // odd part w.r.t. the representative link
+                            (L::D == 3 ? qmul<60>(jz, k.kf[2]) : 0);
+    auto emit = [&](auto I, long long gs) {
+        constexpr int i = decltype(I)::value;
+        const unsigned long long wb = (unsigned long long)k.w_bits[Link<L, i>::cls];
+        const unsigned long long o = wb + (unsigned long long)rne_shift<FixLink<L, i>::SHIFT>(gs);
+        ok &= ((o ^ wb) >> 52) == 0;
+        out[i * stride] = o;
+    };
+    long long R = 0, V = 0, PX = 0, PY = 0, PZ = 0;  // scalars of the current weight class
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         using F = FixLink<L, i>;
         using K = Link<L, i>;
         if constexpr (F::REP == i) {
             constexpr int c = K::cls;
-            const long long Y = K::cx * jx + K::cy * jy + K::cz * jz;
-            const long long A = qmul<59>(Y, k.alpha) + k.beta[i];
-            const long long T = qmul<60>(Y, A);
-            E[i] = R[c] + qmul<60>(T - gamma, V[c]);
-            O[i] = K::cx * PX[c] + K::cy * PY[c] + K::cz * PZ[c] + k.so[i];
+            if constexpr (i == first_of_class<L, c>()) {
+                R = qmul<62>(dr, k.k_rho[c]);
+                V = MODEL == LBM_QUASI_COMPRESSIBLE ? k.w60[c] + qmul<62>(e, k.kw[c]) : k.w60[c];
+                if constexpr (c > 0) {
+                    PX = qmul<61>(jx, k.k_j[c]);
+                    PY = qmul<61>(jy, k.k_j[c]);
+                    if constexpr (L::D == 3) PZ = qmul<61>(jz, k.k_j[c]);
+                }
+            }
+            if constexpr (i == 0) {
+                emit(I, qmul<62>(g[0], k.k_keep) + R + qmul<60>(-gamma, V));
+            } else {
+                constexpr int j = K::opp;
+                const long long Y = K::cx * jx + K::cy * jy + K::cz * jz;
+                const long long A = qmul<59>(Y, k.alpha) + k.beta[i];
+                const long long T = qmul<60>(Y, A);
+                const long long E = R + qmul<60>(T - gamma, V);
+                const long long O = K::cx * PX + K::cy * PY + K::cz * PZ + k.so[i];
+                emit(I, qmul<62>(g[i], k.k_keep) + E + O);
+                emit(std::integral_constant<int, j>{}, qmul<62>(g[j], k.k_keep) + E - O);
+            }
         }
-    });
-    static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        using F = FixLink<L, i>;
-        const long long gs = qmul<62>(g[i], k.k_keep) + E[F::REP] + (F::SIGN > 0 ? O[F::REP] : -O[F::REP]);
-        const unsigned long long wb = (unsigned long long)k.w_bits[Link<L, i>::cls];
-        const unsigned long long out = wb + (unsigned long long)rne_shift<F::SHIFT>(gs);
-        ok &= ((out ^ wb) >> 52) == 0;
-        b[i] = out;
     });
     return ok;
 }
 
-template <class L, int A, int TPB, int MODEL>
-__global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_step_fixed(const StepArgs a) {
+template <class L, int A, int MODEL, int MINB>
+__global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_fixed(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = unsigned long long;
-    constexpr size_t TILE_BYTES = sizeof(T) * L::Q * TL::NT;
-    __shared__ NeighShared<TL, TPB> sh;
-    const int lt = threadIdx.x / TL::NT;
-    const int node = threadIdx.x - lt * TL::NT;
-    const int tile = blockIdx.x * TPB + lt;
-    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, static_cast<const unsigned char*>(a.src), TILE_BYTES,
-                                 a.n_tiles, tile, lt, node);
-    __syncthreads();  // the only barrier (Fig. 5, step 4)
-    if (tile >= a.n_tiles || !mask_bit(sh, lt, TL::CENTER, node)) return;
-
-    const NodePos<A> p = node_pos<TL>(node);
+    __shared__ NeighShared<TL, work_tiles()> sh;
+    WorkNode wn;
+    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    const NodePos<A> p = node_pos<TL>(wn.node);
     T b[L::Q];
-    gather<L, A, TPB, T>(sh, lt, node, p, b);
-    if (!collide_fixed<L, MODEL>(b, a.fx)) {
+    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
+    const int stride = sh.stride[wn.lt][TL::CENTER];
+    T* out = static_cast<T*>(a.dst) +
+             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+    if (!collide_fixed<L, MODEL>(b, a.fx, out, stride)) {
         // out of the fixed-point range: the same update with FP64 instructions
-        gather<L, A, TPB, T>(sh, lt, node, p, b);
+        gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
         double f[L::Q];
-        static_for<0, L::Q>([&](auto I) { f[decltype(I)::value] = __longlong_as_double((long long)b[decltype(I)::value]); });
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[i] = __longlong_as_double((long long)b[i]);
+        });
         collide_f64<L, MODEL>(f, a.omega, a.force);
-        static_for<0, L::Q>([&](auto I) { b[decltype(I)::value] = (T)__double_as_longlong(f[decltype(I)::value]); });
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            out[i * stride] = (T)__double_as_longlong(f[i]);
+        });
     }
-    T* out = static_cast<T*>(a.dst) + (size_t)tile * L::Q * TL::NT + node;
-    static_for<0, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        out[i * TL::NT] = b[i];
-    });
 }
 
-template <class L, int A, int MODEL>
+template <class L, int A, int MODEL, int MINB>
 cudaError_t launch_step_fixed(const StepArgs& a, cudaStream_t s) {
-    constexpr int TPB = tiles_per_block<L, A>();
-    const int blocks = (a.n_tiles + TPB - 1) / TPB;
-    if (blocks == 0) return cudaSuccess;
-    k_step_fixed<L, A, TPB, MODEL><<<blocks, TPB * Tile<L, A>::NT, 0, s>>>(a);
+    if (a.n_work_blocks == 0) return cudaSuccess;
+    k_step_fixed<L, A, MODEL, MINB><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -237,10 +248,27 @@ void fixed_consts(const lbm_params* p, FixedConsts* k) {
         fixed_consts_for<D3Q19>(p, k);
 }
 
+// Resident blocks per SM the compiler is asked to allow (register cap):
+// LBM_FIXED_MINBLOCKS = 1, 2 or 3 (default; measured fastest on GB300).
+static int min_blocks() {
+    const char* v = std::getenv("LBM_FIXED_MINBLOCKS");
+    const int m = v ? std::atoi(v) : 3;
+    return m >= 1 && m <= 3 ? m : 3;
+}
+
+template <class L, int A, int MODEL>
+static StepLaunch pick_minb() {
+    switch (min_blocks()) {
+        case 1: return &launch_step_fixed<L, A, MODEL, 1>;
+        case 2: return &launch_step_fixed<L, A, MODEL, 2>;
+        default: return &launch_step_fixed<L, A, MODEL, 3>;
+    }
+}
+
 template <class L, int A>
 static StepLaunch pick(int model) {
-    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_fixed<L, A, LBM_QUASI_COMPRESSIBLE>
-                                           : &launch_step_fixed<L, A, LBM_INCOMPRESSIBLE>;
+    return model == LBM_QUASI_COMPRESSIBLE ? pick_minb<L, A, LBM_QUASI_COMPRESSIBLE>()
+                                           : pick_minb<L, A, LBM_INCOMPRESSIBLE>();
 }
 
 StepLaunch select_step_fixed(int lattice, int a, int model) {

@@ -5,8 +5,8 @@
 // a thread block.  Before the single barrier, the threads of a tile copy the
 // tile's 3^d neighbour record into shared memory as base pointers of the
 // neighbours' PDF blocks, together with the neighbours' fluid-node bit masks
-// (Fig. 5, steps 1-3: the tile bitmap and the node types of the tile and its
-// halo).  After the barrier every fluid node pulls f*_i(r - c_i) from the
+// (the copy of the tile bitmap and the node types of the tile and its halo
+// that Fig. 5 stages).  After the barrier every fluid node pulls f*_i(r - c_i) from the
 // tile that holds r - c_i, or, when that node is solid, in a removed tile or
 // beyond a wall, its own f*_{opp(i)}(r) (halfway bounce-back).
 #pragma once
@@ -21,20 +21,40 @@ namespace lbm {
 template <class TL, int TPB>
 struct NeighShared {
     const unsigned char* base[TPB][TL::NN];  // PDF block of each neighbour slot
+    int stride[TPB][TL::NN];                 // its values per link
     uint64_t m[TPB][TL::NN][TL::W];          // its fluid-node bits (0 when removed)
 };
+
+// Rank of node n among the fluid nodes of a tile (its slot in the compact
+// layout): the number of fluid bits below bit n.
+template <int W>
+__device__ __forceinline__ int fluid_rank(const uint64_t* m, int n) {
+    const int w = n >> 6;
+    int r = __popcll(m[w] & ((1ull << (n & 63)) - 1ull));
+    if constexpr (W > 1) {
+#pragma unroll
+        for (int k = 0; k < W - 1; k++)
+            if (k < w) r += __popcll(m[k]);
+    }
+    return r;
+}
 
 // Threads of one tile cooperatively stage the neighbourhood of `tile`.
 template <class TL, int TPB>
 __device__ __forceinline__ void stage_neighbourhood(NeighShared<TL, TPB>& sh, const int32_t* __restrict__ nbr,
                                                     const uint64_t* __restrict__ tmask,
-                                                    const unsigned char* pdf, size_t tile_bytes, int n_tiles,
+                                                    const long long* __restrict__ tile_off,
+                                                    const int32_t* __restrict__ tile_stride,
+                                                    const unsigned char* pdf, int value_bytes, int n_tiles,
                                                     int tile, int lt, int node) {
     for (int k = node; k < TL::NN * TL::W; k += TL::NT) {
         const int slot = k / TL::W, w = k - slot * TL::W;
         const int nb = tile < n_tiles ? __ldg(nbr + (size_t)tile * TL::NN + slot) : -1;
         sh.m[lt][slot][w] = nb >= 0 ? __ldg(tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0) sh.base[lt][slot] = pdf + (size_t)(nb >= 0 ? nb : 0) * tile_bytes;
+        if (w == 0) {
+            sh.base[lt][slot] = pdf + (nb >= 0 ? __ldg(tile_off + nb) : 0ll) * value_bytes;
+            sh.stride[lt][slot] = nb >= 0 ? __ldg(tile_stride + nb) : 0;
+        }
     }
 }
 
@@ -78,21 +98,26 @@ struct PullSource {
     }
 };
 
-// Gather the q post-collision words that arrive at `node` (raw storage words).
+// Gather the q post-collision words that arrive at `node` (raw storage words)
+// from the compact blocks; returns the node's own slot (its fluid rank).
 template <class L, int A, int TPB, class T>
-__device__ __forceinline__ void gather(const NeighShared<Tile<L, A>, TPB>& sh, int lt, int node,
-                                       const NodePos<A>& p, T (&f)[L::Q]) {
+__device__ __forceinline__ int gather(const NeighShared<Tile<L, A>, TPB>& sh, int lt, int node,
+                                      const NodePos<A>& p, T (&f)[L::Q]) {
     using TL = Tile<L, A>;
     const T* own = reinterpret_cast<const T*>(sh.base[lt][TL::CENTER]);
-    f[0] = __ldg(own + node);
+    const int own_stride = sh.stride[lt][TL::CENTER];
+    const int own_rank = fluid_rank<TL::W>(sh.m[lt][TL::CENTER], node);
+    f[0] = __ldg(own + own_rank);
     static_for<1, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const PullSource<L, A, i> s(p);
         const bool fl = mask_bit(sh, lt, s.slot, s.sn);
-        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * TL::NT + s.sn
-                          : own + Link<L, i>::opp * TL::NT + node;
+        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * sh.stride[lt][s.slot] +
+                                fluid_rank<TL::W>(sh.m[lt][s.slot], s.sn)
+                          : own + Link<L, i>::opp * own_stride + own_rank;
         f[i] = __ldg(src);
     });
+    return own_rank;
 }
 
 // ---- storage policies: raw words <-> FP64 values ------------------------------
@@ -114,6 +139,20 @@ struct StoreF32 {
     __device__ static __forceinline__ T from_f64(double v, double) { return __float_as_uint((float)v); }
 };
 
+// FP32 holding the deviation f_i - w_i.
+struct StoreF32S {
+    using T = unsigned int;
+    static constexpr int id = LBM_STORE_F32S;
+    template <class L, int I>
+    __device__ static __forceinline__ double to_f64(T r, double) {
+        return Link<L, I>::w + (double)__uint_as_float(r);
+    }
+    template <class L, int I>
+    __device__ static __forceinline__ T from_f64(double v, double) {
+        return __float_as_uint((float)(v - Link<L, I>::w));
+    }
+};
+
 // FP16 holding the scaled deviation (f_i - w_i) * scale.
 struct StoreF16S {
     using T = unsigned short;
@@ -131,6 +170,48 @@ struct StoreF16S {
 template <class L, int A>
 constexpr int tiles_per_block() {
     return Tile<L, A>::NT >= 256 ? 1 : 256 / Tile<L, A>::NT;
+}
+
+// ---- work lists: one thread per fluid node ------------------------------------
+// The host packs the fluid nodes of consecutive tiles into blocks of at most
+// work_threads<L,A>() nodes and work_tiles() tiles (see WorkBlock in
+// internal.h), so no lane of the step kernels idles on a solid node.
+template <class L, int A>
+constexpr int work_threads() {
+    return Tile<L, A>::NT > 256 ? Tile<L, A>::NT : 256;
+}
+constexpr int work_tiles() { return 16; }
+
+struct WorkNode {
+    int lt, tile, node;
+};
+
+// Stage the neighbourhoods of the block's tiles, then decode this thread's
+// fluid node.  Every thread of the block must call it (it holds the barrier);
+// returns false for threads beyond the block's node count.
+template <class TL, int KMAX>
+__device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
+                                           WorkNode& wn) {
+    const WorkBlock wb = a.blocks[blockIdx.x];
+    const unsigned char* pdf = static_cast<const unsigned char*>(a.src);
+    for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
+        const int lt = k / (TL::NN * TL::W);
+        const int r = k - lt * (TL::NN * TL::W);
+        const int slot = r / TL::W, w = r - slot * TL::W;
+        const int nb = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
+        sh.m[lt][slot][w] = nb >= 0 ? __ldg(a.tmask + (size_t)nb * TL::W + w) : 0ull;
+        if (w == 0) {
+            sh.base[lt][slot] = pdf + (nb >= 0 ? __ldg(a.tile_off + nb) : 0ll) * value_bytes;
+            sh.stride[lt][slot] = nb >= 0 ? __ldg(a.tile_stride + nb) : 0;
+        }
+    }
+    __syncthreads();  // the only barrier of the step (Fig. 5)
+    if ((int)threadIdx.x >= wb.count) return false;
+    const uint32_t e = __ldg(a.nodes + wb.node_begin + threadIdx.x);
+    wn.tile = (int)(e >> (TL::D * TL::LA));
+    wn.node = (int)(e & (TL::NT - 1));
+    wn.lt = wn.tile - wb.tile_begin;
+    return true;
 }
 
 }  // namespace lbm

@@ -8,6 +8,9 @@
 // Each non-empty tile also gets the 3^d record of its neighbours' indices
 // (the local copy of the tile bitmap in Fig. 5) and a bit mask of its fluid
 // nodes (one bit per node instead of the paper's s_t = 2 bytes, Eq. 21).
+// PDFs are stored compactly: a tile's block holds only its fluid nodes (in
+// row order), so solid nodes of porous tiles cost neither memory nor
+// bandwidth; a node's slot is its rank among the tile's fluid nodes.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -40,6 +43,7 @@ size_t bytes_per_value(int storage) {
     switch (storage) {
         case LBM_STORE_F64: return 8;
         case LBM_STORE_F32: return 4;
+        case LBM_STORE_F32S: return 4;
         case LBM_STORE_F16S: return 2;
         default: return 0;
     }
@@ -81,6 +85,8 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     const int ntx = (nx + a - 1) / a, nty = (ny + a - 1) / a, ntz = d == 3 ? (nz + a - 1) / a : 1;
     const int64_t n_tiles64 = (int64_t)ntx * nty * ntz;
     if (n_tiles64 > INT32_MAX) return fail(LBM_ERR_CAPACITY, "too many tiles");
+    if (n_tiles64 * a * a * (d == 3 ? a : 1) > (int64_t)UINT32_MAX)
+        return fail(LBM_ERR_CAPACITY, "too many tile slots for 32-bit node indices");
     const int nt = a * a * az;
     T->a = a;
     T->d = d;
@@ -151,6 +157,22 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
                 }
     }
 
+    // Compact layout: a tile stores only its fluid nodes, in row order, link
+    // after link with no padding (contiguous link arrays fill whole sectors).
+    const int bpv = (int)bytes_per_value(p->storage);
+    const int pad = 1;
+    T->tile_off.resize(count);
+    T->tile_stride.resize(count);
+    long long total = 0;
+    for (int32_t k = 0; k < count; k++) {
+        int nf = 0;
+        for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(T->tmask[(size_t)k * T->words + w]);
+        const int stride = (nf + pad - 1) / pad * pad;
+        T->tile_off[k] = total;
+        T->tile_stride[k] = stride;
+        total += (long long)lattice_q(p->lattice) * stride;
+    }
+
     lbm_tiling& I = T->info;
     I.ntx = ntx;
     I.nty = nty;
@@ -159,8 +181,42 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     I.n_ftiles = count;
     I.nbr_per_tile = T->nn;
     I.n_fluid = n_fluid;
-    I.pdf_bytes = (size_t)count * lattice_q(p->lattice) * nt * bytes_per_value(p->storage);
+    I.pdf_bytes = (size_t)total * bpv;
     return LBM_OK;
+}
+
+int work_threads_for(int lattice, int a) {
+    const int nt = lattice == LBM_D2Q9 ? a * a : a * a * a;
+    return nt > 256 ? nt : 256;
+}
+
+// Fluid nodes in tile-major, row order, cut into blocks of consecutive tiles
+// holding at most `threads` nodes and `max_tiles` tiles.
+void build_work_list(HostTiling* T, int threads, int max_tiles) {
+    const int nt = T->d == 3 ? T->a * T->a * T->a : T->a * T->a;
+    const int32_t n = T->info.n_ftiles;
+    T->nodes.clear();
+    T->blocks.clear();
+    T->nodes.reserve((size_t)T->info.n_fluid);
+    WorkBlock cur{0, 0, 0, 0};
+    for (int32_t k = 0; k < n; k++) {
+        const uint64_t* m = &T->tmask[(size_t)k * T->words];
+        int nf = 0;
+        for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(m[w]);
+        if (cur.n_tiles > 0 && (cur.count + nf > threads || cur.n_tiles == max_tiles)) {
+            T->blocks.push_back(cur);
+            cur = WorkBlock{0, 0, 0, 0};
+        }
+        if (cur.n_tiles == 0) {
+            cur.node_begin = (int)T->nodes.size();
+            cur.tile_begin = k;
+        }
+        for (int node = 0; node < nt; node++)
+            if ((m[node >> 6] >> (node & 63)) & 1ull) T->nodes.push_back((uint32_t)k * (uint32_t)nt + node);
+        cur.count += nf;
+        cur.n_tiles++;
+    }
+    if (cur.n_tiles > 0) T->blocks.push_back(cur);
 }
 
 }  // namespace lbm

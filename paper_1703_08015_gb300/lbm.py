@@ -20,7 +20,7 @@ ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_SHAPE", -3: "LBM_ERR_CUDA", -4: "LBM_E
           -5: "LBM_ERR_DIVERGED", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_BOUNDS", -8: "LBM_ERR_CAPACITY"}
 LBM_D2Q9, LBM_D3Q19 = 9, 19
 LBM_QUASI_COMPRESSIBLE, LBM_INCOMPRESSIBLE = 0, 1
-LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S = 0, 1, 2
+LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S, LBM_STORE_F32S = 0, 1, 2, 3
 LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED = 0, 1, 2
 LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
 

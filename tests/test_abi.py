@@ -44,8 +44,8 @@ def _check_tiling(mask, lattice, a, periodic):
     assert info.n_ftiles == rmask.shape[0]
     assert info.n_tiles == rtm.size
     assert info.n_fluid == int(np.count_nonzero(mask))
-    q = lattice
-    assert info.pdf_bytes == info.n_ftiles * q * a ** dim * 8
+    # compact layout: each tile stores only its fluid nodes, q links each
+    assert info.pdf_bytes == int(rmask.sum()) * lattice * 8
 
 
 @pytest.mark.parametrize("seed", range(8))
