@@ -72,12 +72,13 @@ extern "C" {
 #define LBM_STORE_F16S 2 /* FP16 scaled deviations (f_i - w_i) * S, FP32 collision (not in the paper) */
 #define LBM_STORE_F32S 3 /* FP32 deviations f_i - w_i, FP32 collision (not in the paper) */
 
-/* Arithmetic of the FP64 step.  Both variants compute the same update; they
- * differ only in rounding (see lbm_step). */
-#define LBM_ARITH_AUTO   0 /* = LBM_ARITH_FIXED */
+/* Arithmetic of the FP64 step.  All variants compute the same FP64 update;
+ * they differ only in rounding (see lbm_step).  Nodes outside the range of
+ * the fixed-point and float-float forms fall back to native FP64. */
+#define LBM_ARITH_AUTO   0 /* = LBM_ARITH_FF */
 #define LBM_ARITH_F64    1 /* native FP64 instructions */
-#define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions;
-                              nodes outside its range fall back to FP64 */
+#define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions */
+#define LBM_ARITH_FF     3 /* exact integer sums, float-float products (~48 bits), no FP64 instructions */
 
 /* lbm_moments flags */
 #define LBM_OUT_DEVICE    1 /* rho/u/pdf pointers are device pointers (default: host) */
@@ -99,6 +100,11 @@ typedef struct lbm_params {
     int arith;        /* LBM_ARITH_* (LBM_STORE_F64 only) */
     double f16_scale; /* LBM_STORE_F16S: scale S of the deviations (a power of two
                          keeps the scaling exact); 0 = default 2^16 */
+    int block_nodes;  /* fluid nodes per step-kernel block: 0 = default (256, or a^d
+                         when a tile has more nodes); 128 is also compiled for the
+                         FP32 storage forms with 4^3 / 8^2 tiles (autotuner choice) */
+    int persistent;   /* 1 = FP32 storage forms run a persistent step kernel: as many
+                         blocks as fit on the GPU at once loop over the work list */
 } lbm_params;
 
 typedef struct lbm_tiling {
@@ -166,15 +172,17 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
  * (propagation only between non-solid nodes, Sec. 3.2: halfway bounce-back),
  * collides, and stores into the other copy; the copies then swap (Sec. 3).
  * Asynchronous on `stream`.  With LBM_ARITH_FIXED the FP64 update is computed
- * with 64-bit fixed-point integers (resolution 2^-60) and rounded once to
- * FP64; it agrees with LBM_ARITH_F64 to rounding.
+ * with 64-bit fixed-point integers (resolution 2^-60), with LBM_ARITH_FF
+ * with exact integer sums and float-float products; either is rounded once to
+ * FP64 and agrees with LBM_ARITH_F64 to rounding.
  * Errors: LBM_ERR_ARG (NULL ctx, nsteps < 0), LBM_ERR_CUDA. */
 int lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 
 /* Density and velocity that the next step will collide with (the gathered
  * values; rho = sum f_i, u from Eq. 5 / Eq. 6 with the F/2 correction), and
- * FP64 reductions over the fluid nodes in a fixed order (deterministic).
- *   rho    dense nx*ny*nz doubles or NULL; solid nodes get NaN.
+ * FP64 reductions over the fluid nodes in a fixed order (deterministic; for a
+ * batch the sums run over all samples, in sample order).
+ *   rho    dense nx*ny*nz doubles or NULL (single geometry only); NaN at solid.
  *   u      dense 3*nx*ny*nz doubles [component][z][y][x] or NULL; NaN at solid.
  *   stats  host, or NULL.
  *   flags  LBM_OUT_DEVICE: rho and u are device pointers (default host);
@@ -187,12 +195,14 @@ int lbm_moments(lbm_ctx* ctx, double* rho, double* u, lbm_stats* stats,
 
 /* Copy the current post-collision PDFs out as a dense FP64 array
  * [i][z][y][x] (q * nx*ny*nz doubles; solid nodes NaN), host or device
- * (LBM_OUT_DEVICE).  Used for checkpoints and for checking the step.
+ * (LBM_OUT_DEVICE).  Used for checkpoints and for checking the step.  Single
+ * geometry only (a batch uses lbm_export_pdfs_sample).
  * Synchronises `stream` for host output.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_export_pdfs(lbm_ctx* ctx, double* pdfs, int flags, void* stream);
 
 /* Overwrite the current post-collision PDFs from a dense FP64 array laid out
- * as in lbm_export_pdfs (values at solid nodes are ignored); `step` becomes
+ * as in lbm_export_pdfs (values at solid nodes are ignored; single geometry
+ * only); `step` becomes
  * the context's step count.  Resuming from an exported state reproduces an
  * uninterrupted run bit for bit.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
@@ -229,6 +239,40 @@ int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
  * Calls no cudaMalloc, cudaFree or allocating library routine.
  * Errors: LBM_ERR_ARG, LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
 int lbm_stats_noalloc(const lbm_ctx* ctx, double* stats_dev, void* stream);
+
+/* ---- batches of geometries (not in the paper) ------------------------------
+ * Many independent samples of uneven size and sparsity advance together: each
+ * sample is tiled on its own and the tiles of all samples form one
+ * concatenated list (one work list, one launch per step; with
+ * params->persistent a grid of resident blocks loops over it).  lbm_step
+ * applies to a batch unchanged; moments and exports are per sample.  All
+ * samples share params (lattice, tile edge, periodic axes, tau, force,
+ * storage); params->nx/ny/nz are ignored.
+ *   dims   host, n_samples * 3 ints: nx, ny, nz of each sample.
+ *   masks  host, n_samples pointers to [z][y][x] masks (nonzero = fluid). */
+
+/* Counts summed over the samples and the bytes of one PDF copy of the batch.
+ * Errors: LBM_ERR_ARG, LBM_ERR_SHAPE (a sample's periodic axis), LBM_ERR_CAPACITY. */
+int lbm_build_tilemap_batch(const lbm_params* p, int n_samples, const int* dims,
+                            const uint8_t* const* masks, lbm_tiling* out);
+
+/* Like lbm_init for a batch (every sample starts at rest with density rho0).
+ * Errors: as lbm_init. */
+int lbm_init_batch(lbm_ctx** out, const lbm_params* p, int n_samples, const int* dims,
+                   const uint8_t* const* masks, void* pdf_a, void* pdf_b, size_t pdf_bytes,
+                   void* stream);
+
+/* Per-sample statistics: stats[k] for sample k (as lbm_moments; the residual
+ * uses each sample's own sums).  Synchronises `stream`.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_DIVERGED (some sample). */
+int lbm_moments_batch(lbm_ctx* ctx, lbm_stats* stats, int flags, void* stream);
+
+/* lbm_export_pdfs for sample k of a batch (dense over that sample's box).
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_export_pdfs_sample(lbm_ctx* ctx, int sample, double* pdfs, int flags, void* stream);
+
+/* Number of samples in the context (1 for lbm_init); 0 for NULL. */
+int lbm_num_samples(const lbm_ctx* ctx);
 
 /* Counts of the context's tiling (see lbm_tiling).  Errors: LBM_ERR_ARG. */
 int lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out);

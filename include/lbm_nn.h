@@ -1,0 +1,81 @@
+/*
+ * lbm_nn.h -- C ABI of the learned warm start (not in the paper).
+ *
+ * A small 3D convolutional network predicts an initial density and velocity
+ * field from a geometry mask so that the lattice Boltzmann solve reaches its
+ * steady state in fewer steps; the LBM residual alone still decides
+ * convergence.  These entry points are the network's GPU kernels: 3x3x3
+ * convolutions on tensor cores (BF16 operands, FP32 accumulation) for the
+ * forward pass and both backward passes, plus the pooling, upsampling,
+ * concatenation, loss and optimiser steps of training.
+ *
+ * Conventions
+ *   - Activations are channels-last BF16 (or FP32 where stated) tensors
+ *     [n][z][y][x][c] with dims n, d (z), h (y), w (x) and c channels.
+ *   - Convolution weights are BF16 [27][cin][cout] (tap = 9 dz + 3 dy + dx,
+ *     offsets dz, dy, dx in 0..2 meaning -1, 0, +1), zero padding 1, stride 1.
+ *   - Every pointer is a device pointer; `stream` is a cudaStream_t.  Calls are
+ *     asynchronous.  Return LBM_OK (0) or LBM_ERR_ARG / LBM_ERR_CUDA (lbm.h);
+ *     lbm_last_error() has the message.
+ */
+#ifndef LBM_NN_H
+#define LBM_NN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* y[p][co] = act( sum_{tap,ci} wgt[tap][ci][co] * x[p + off(tap)][ci] + bias[co] ),
+ * act = ReLU when relu != 0.  Output BF16 (y) and/or FP32 (y32); either may
+ * be NULL.  cout <= 128.  The backward-data pass is this same call on dy with
+ * the weights from lbm_nn_weight_flip. */
+int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
+                  const float* bias, int cout, int relu, void* y, float* y32, void* stream);
+
+/* dx-ready weights: wt[tap][co][ci] = wgt[26 - tap][ci][co] (BF16). */
+int lbm_nn_weight_flip(const void* wgt, int cin, int cout, void* wt, void* stream);
+
+/* dw[tap][ci][co] += sum_p x[p + off(tap)][ci] * dy[p][co] and, when dbias
+ * is not NULL, dbias[co] += sum_p dy[p][co] (FP32 accumulators). */
+int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout,
+                        float* dw, float* dbias, void* stream);
+
+/* g[i] *= (act[i] > 0), over count BF16 values (ReLU backward in place). */
+int lbm_nn_relu_mask(void* g, const void* act, size_t count, void* stream);
+
+/* 2x2x2 average pooling (d, h, w even) and its adjoint. */
+int lbm_nn_pool2(const void* x, int n, int d, int h, int w, int c, void* y, void* stream);
+int lbm_nn_pool2_bwd(const void* dy, int n, int d, int h, int w, int c, void* dx, void* stream);
+
+/* Nearest-neighbour upsampling by 2 (input dims given) and its adjoint. */
+int lbm_nn_up2(const void* x, int n, int d, int h, int w, int c, void* y, void* stream);
+int lbm_nn_up2_bwd(const void* dy, int n, int d, int h, int w, int c, void* dx, void* stream);
+
+/* Channel concatenation y = [a | b] over `voxels` voxels, and its split. */
+int lbm_nn_concat(const void* a, int ca, const void* b, int cb, size_t voxels, void* y, void* stream);
+int lbm_nn_split(const void* y, int ca, int cb, size_t voxels, void* a, void* b, void* stream);
+
+/* Masked mean-squared error of FP32 predictions against FP32 targets over
+ * `voxels` voxels of c channels where mask[p] != 0 (`count` such voxels):
+ * loss (device, 1 double, overwritten) and dpred = 2 (pred - target) mask /
+ * (count * c) as BF16. */
+int lbm_nn_mse(const float* pred, const float* target, const uint8_t* mask, size_t voxels, int c,
+               size_t count, double* loss, void* dpred, void* stream);
+
+/* One Adam step on FP32 master weights p with gradient g (then zeroed), moment
+ * buffers m, v, writing the BF16 copy pb.  t is the step number (1-based). */
+int lbm_nn_adam(float* p, float* g, float* m, float* v, void* pb, size_t count, float lr, float beta1,
+                float beta2, float eps, int t, void* stream);
+
+/* Format conversions. */
+int lbm_nn_f32_to_bf16(const float* x, size_t count, void* y, void* stream);
+int lbm_nn_bf16_to_f32(const void* x, size_t count, float* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_NN_H */

@@ -2,6 +2,7 @@
 // captured CUDA graph of several steps), moments and PDF export/import.
 #include <cmath>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -10,15 +11,21 @@
 namespace lbm {
 StepLaunch select_step_f64(int lattice, int a, int model, int storage);
 StepLaunch select_step_fixed(int lattice, int a, int model);
-StepLaunch select_step_f32(int lattice, int a, int model, int storage);
+StepLaunch select_step_f32(int lattice, int a, int model, int storage, int block_nodes, int persistent);
 
-StepLaunch select_step(int lattice, int a, int model, int storage, int arith) {
+StepLaunch select_step_ff(int lattice, int a, int model);
+
+StepLaunch select_step(const lbm_params* p) {
+    const int lattice = p->lattice, a = p->tile_a, model = p->model, storage = p->storage, arith = p->arith;
     if (storage == LBM_STORE_F64) {
+        if (p->persistent || (p->block_nodes && p->block_nodes != work_threads_for(lattice, a))) return nullptr;
+        StepLaunch f = nullptr;
         if (arith == LBM_ARITH_F64) return select_step_f64(lattice, a, model, storage);
-        StepLaunch f = select_step_fixed(lattice, a, model);
+        if (arith == LBM_ARITH_FIXED) f = select_step_fixed(lattice, a, model);
+        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO) f = select_step_ff(lattice, a, model);
         return f ? f : select_step_f64(lattice, a, model, storage);
     }
-    return select_step_f32(lattice, a, model, storage);
+    return select_step_f32(lattice, a, model, storage, p->block_nodes, p->persistent);
 }
 }  // namespace lbm
 
@@ -47,6 +54,8 @@ struct lbm_ctx {
     size_t stage_bytes = 0;
     int nblocks = 0;            // blocks of the node kernels (= partial sums)
     bool u_saved_valid = false;
+    std::vector<SampleRange> samples;     // one entry per geometry of a batch
+    std::vector<int> part_begin, part_blocks;  // their slices of the partial sums
     StepArgs sa{};
     NodeArgs na{};
     StepLaunch step_fn = nullptr;
@@ -127,19 +136,13 @@ static int ensure_stage(lbm_ctx* c, size_t bytes) {
     return LBM_OK;
 }
 
-extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask, void* pdf_a, void* pdf_b,
-                        size_t pdf_bytes, const double* rho_init, const double* u_init, void* stream) {
-    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    int rc = validate_params(p);
-    if (rc) return rc;
+static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std::vector<SampleRange>& samples,
+                    void* pdf_a, void* pdf_b, size_t pdf_bytes, const double* rho_init, const double* u_init,
+                    void* stream) {
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBM_ERR_ARG, "tau must be > 1/2");
     if (!pdf_a || !pdf_b || pdf_a == pdf_b) return fail(LBM_ERR_ARG, "two distinct PDF buffers are required");
     if ((reinterpret_cast<uintptr_t>(pdf_a) | reinterpret_cast<uintptr_t>(pdf_b)) & 255)
         return fail(LBM_ERR_ARG, "PDF buffers must be 256-byte aligned");
-    HostTiling T;
-    rc = build_tiling(p, mask, &T);
-    if (rc) return rc;
     if (pdf_bytes < T.info.pdf_bytes)
         return fail(LBM_ERR_ARG, "PDF buffers hold %zu bytes, %zu needed", pdf_bytes, T.info.pdf_bytes);
 
@@ -148,6 +151,7 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     c->p = *p;
     if (c->p.storage == LBM_STORE_F16S && !(c->p.f16_scale > 0.0)) c->p.f16_scale = 65536.0;
     c->info = T.info;
+    c->samples = samples;
     c->q = lattice_q(p->lattice);
     c->nt = T.a * T.a * (T.d == 3 ? T.a : 1);
     c->pdf[0] = pdf_a;
@@ -156,20 +160,28 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     const char* env = std::getenv("LBM_NO_GRAPH");
     c->use_graph = !(env && env[0] == '1');
 
-    c->step_fn = select_step(p->lattice, p->tile_a, p->model, p->storage, p->arith);
+    c->step_fn = select_step(p);
     NodeLaunch init_fn = select_init(p->lattice, p->tile_a, p->model, p->storage);
     c->moments_fn = select_moments(p->lattice, p->tile_a, p->model, p->storage);
     c->export_fn = select_export(p->lattice, p->tile_a, p->storage);
     c->import_fn = select_import(p->lattice, p->tile_a, p->storage);
     if (!c->step_fn || !init_fn || !c->moments_fn || !c->export_fn || !c->import_fn) {
         release(c);
-        return fail(LBM_ERR_ARG, "no kernel for lattice %d, tile %d, model %d, storage %d", p->lattice,
-                    p->tile_a, p->model, p->storage);
+        return fail(LBM_ERR_ARG, "no kernel for lattice %d, tile %d, model %d, storage %d, block %d, persistent %d",
+                    p->lattice, p->tile_a, p->model, p->storage, p->block_nodes, p->persistent);
     }
 
     cudaStream_t s = S(stream);
     const int nf = T.info.n_ftiles;
+    // partial sums: one launch over all tiles (lbm_stats_noalloc) or one per sample
     c->nblocks = node_blocks(p->lattice, p->tile_a, nf);
+    int acc = 0;
+    for (const SampleRange& r : samples) {
+        c->part_begin.push_back(acc);
+        c->part_blocks.push_back(node_blocks(p->lattice, p->tile_a, r.n_tiles));
+        acc += c->part_blocks.back();
+    }
+    const int n_partials = std::max(std::max(c->nblocks, acc), 1);
 #define TRY(x)                \
     do {                      \
         int r_ = (x);         \
@@ -186,13 +198,13 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     TRY(upload(&c->d_nbr, T.nbr, s));
     TRY(upload(&c->d_tmask, T.tmask, s));
     TRY(upload(&c->d_coords, T.coords, s));
-    build_work_list(&T, work_threads_for(p->lattice, p->tile_a), 16);
+    build_work_list(&T, p->block_nodes ? p->block_nodes : work_threads_for(p->lattice, p->tile_a), 16);
     TRY(upload(&c->d_nodes, T.nodes, s));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
     TRY(upload(&c->d_tile_stride, T.tile_stride, s));
-    CTRY(cudaMalloc(&c->d_partials, (size_t)(c->nblocks > 0 ? c->nblocks : 1) * 8 * sizeof(double)));
-    CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double)));
+    CTRY(cudaMalloc(&c->d_partials, (size_t)n_partials * 8 * sizeof(double)));
+    CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double) * samples.size()));
     CTRY(cudaMalloc(&c->d_err, sizeof(int)));
     CTRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     CTRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
@@ -217,44 +229,54 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     sa.f16_inv_scale_f = (float)sa.f16_inv_scale;
     sa.err = c->d_err;
     fixed_consts(&c->p, &sa.fx);
+    ff_consts(&c->p, &sa.ffc);
 
-    NodeArgs& na = c->na;
+    NodeArgs& na = c->na;  // a launch over every tile; sample launches narrow it
     na.nbr = c->d_nbr;
     na.tmask = c->d_tmask;
     na.coords = c->d_coords;
     na.tile_off = c->d_tile_off;
     na.tile_stride = c->d_tile_stride;
+    na.tile_begin = 0;
     na.n_tiles = nf;
-    na.nx = p->nx;
-    na.ny = p->ny;
-    na.nz = p->nz;
+    na.nx = samples[0].nx;
+    na.ny = samples[0].ny;
+    na.nz = samples[0].nz;
     for (int k = 0; k < 3; k++) na.force[k] = sa.force[k];
     na.rho0 = p->rho0;
     na.f16_scale = sa.f16_scale;
     na.f16_inv_scale = sa.f16_inv_scale;
     na.partials = c->d_partials;
 
-    // equilibrium start in copy 0; copy 1 is zeroed (its solid slots are never read)
-    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    // equilibrium start in copy 0; copy 1 is zeroed
+    const SampleRange& r0 = samples[0];
+    const size_t N0 = (size_t)r0.nx * r0.ny * r0.nz;
     double* d_rho = nullptr;
     double* d_u = nullptr;
     if (rho_init || u_init) {
-        TRY(ensure_stage(c, N * 4 * sizeof(double)));
+        TRY(ensure_stage(c, N0 * 4 * sizeof(double)));
         if (rho_init) {
             d_rho = c->d_stage;
-            CTRY(cudaMemcpyAsync(d_rho, rho_init, N * sizeof(double), cudaMemcpyHostToDevice, s));
+            CTRY(cudaMemcpyAsync(d_rho, rho_init, N0 * sizeof(double), cudaMemcpyHostToDevice, s));
         }
         if (u_init) {
-            d_u = c->d_stage + N;
-            const size_t nu = (size_t)(p->lattice == LBM_D3Q19 ? 3 : 2) * N;
+            d_u = c->d_stage + N0;
+            const size_t nu = (size_t)(p->lattice == LBM_D3Q19 ? 3 : 2) * N0;
             CTRY(cudaMemcpyAsync(d_u, u_init, nu * sizeof(double), cudaMemcpyHostToDevice, s));
         }
     }
-    NodeArgs ia = na;
-    ia.pdf = pdf_a;
-    ia.rho_in = d_rho;
-    ia.u_in = d_u;
-    CTRY(init_fn(ia, s));
+    for (size_t k = 0; k < samples.size(); k++) {
+        NodeArgs ia = na;
+        ia.pdf = pdf_a;
+        ia.tile_begin = samples[k].tile_begin;
+        ia.n_tiles = samples[k].n_tiles;
+        ia.nx = samples[k].nx;
+        ia.ny = samples[k].ny;
+        ia.nz = samples[k].nz;
+        ia.rho_in = k == 0 ? d_rho : nullptr;
+        ia.u_in = k == 0 ? d_u : nullptr;
+        CTRY(init_fn(ia, s));
+    }
     CTRY(cudaMemsetAsync(pdf_b, 0, T.info.pdf_bytes, s));
     if (rho_init || u_init) CTRY(cudaStreamSynchronize(s));
 #undef CTRY
@@ -262,6 +284,29 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     c->cur = 0;
     *out = c;
     return LBM_OK;
+}
+
+extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask, void* pdf_a, void* pdf_b,
+                        size_t pdf_bytes, const double* rho_init, const double* u_init, void* stream) {
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    HostTiling T;
+    int rc = build_tiling(p, mask, &T);
+    if (rc) return rc;
+    std::vector<SampleRange> samples{SampleRange{p->nx, p->ny, p->nz, 0, T.info.n_ftiles, T.info.n_fluid}};
+    return init_ctx(out, p, T, samples, pdf_a, pdf_b, pdf_bytes, rho_init, u_init, stream);
+}
+
+extern "C" int lbm_init_batch(lbm_ctx** out, const lbm_params* p, int n_samples, const int* dims,
+                              const uint8_t* const* masks, void* pdf_a, void* pdf_b, size_t pdf_bytes,
+                              void* stream) {
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    HostTiling T;
+    std::vector<SampleRange> samples;
+    int rc = build_batch_tiling(p, n_samples, dims, masks, &T, &samples);
+    if (rc) return rc;
+    return init_ctx(out, p, T, samples, pdf_a, pdf_b, pdf_bytes, nullptr, nullptr, stream);
 }
 
 extern "C" int lbm_step(lbm_ctx* c, int nsteps, void* stream) {
@@ -288,8 +333,57 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps, void* stream) {
     return LBM_OK;
 }
 
+static NodeArgs sample_args(const lbm_ctx* c, size_t k) {
+    NodeArgs a = c->na;
+    const SampleRange& r = c->samples[k];
+    a.pdf = c->pdf[c->cur];
+    a.tile_begin = r.tile_begin;
+    a.n_tiles = r.n_tiles;
+    a.nx = r.nx;
+    a.ny = r.ny;
+    a.nz = r.nz;
+    return a;
+}
+
+// Moments of every sample (fields only for a single sample), each reduced in
+// a fixed order into d_result[8k .. 8k+7].
+static int launch_sample_moments(lbm_ctx* c, double* d_rho, double* d_u, bool residual, cudaStream_t s) {
+    if (residual && !c->d_u_saved)
+        LBM_CUDA_TRY(cudaMalloc(&c->d_u_saved, (size_t)c->info.n_ftiles * 3 * c->nt * sizeof(double) + 8));
+    for (size_t k = 0; k < c->samples.size(); k++) {
+        NodeArgs a = sample_args(c, k);
+        a.rho_out = d_rho;
+        a.u_out = d_u;
+        a.residual = residual ? 1 : 0;
+        a.u_saved = residual ? c->d_u_saved : nullptr;
+        a.partials = c->d_partials + (size_t)8 * c->part_begin[k];
+        LBM_CUDA_TRY(c->moments_fn(a, s));
+        LBM_CUDA_TRY(launch_reduce(a.partials, c->part_blocks[k], c->d_result + 8 * k, s));
+    }
+    return LBM_OK;
+}
+
+static void fill_stats(const lbm_ctx* c, const double* r, bool residual, bool had_saved, lbm_stats* st) {
+    st->mass = r[0];
+    st->momentum[0] = r[1];
+    st->momentum[1] = r[2];
+    st->momentum[2] = r[3];
+    st->u2 = r[4];
+    st->du2 = residual ? r[5] : 0.0;
+    st->residual = residual && had_saved && r[4] > 0 ? std::sqrt(r[5] / r[4]) : INFINITY;
+    st->n_fluid = (int64_t)r[6];
+    st->step = c->step;
+}
+
+static bool finite_stats(const lbm_stats& st) {
+    return std::isfinite(st.mass) && std::isfinite(st.momentum[0]) && std::isfinite(st.momentum[1]) &&
+           std::isfinite(st.momentum[2]);
+}
+
 extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* u, lbm_stats* stats, int flags, void* stream) {
     if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+    if ((rho || u) && c->samples.size() != 1)
+        return fail(LBM_ERR_ARG, "rho/u fields need a single-geometry context");
     cudaStream_t s = S(stream);
     const size_t N = (size_t)c->p.nx * c->p.ny * c->p.nz;
     const int d = c->p.lattice == LBM_D3Q19 ? 3 : 2;
@@ -310,45 +404,53 @@ extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* u, lbm_stats* stats,
         if (d_rho) LBM_CUDA_TRY(launch_fill_nan(d_rho, N, s));
         if (d_u) LBM_CUDA_TRY(launch_fill_nan(d_u, d * N, s));
     }
-    if (residual && !c->d_u_saved)
-        LBM_CUDA_TRY(cudaMalloc(&c->d_u_saved, (size_t)c->info.n_ftiles * 3 * c->nt * sizeof(double) + 8));
-    NodeArgs a = c->na;
-    a.pdf = c->pdf[c->cur];
-    a.rho_out = d_rho;
-    a.u_out = d_u;
-    a.residual = residual ? 1 : 0;
-    a.u_saved = residual ? c->d_u_saved : nullptr;
-    LBM_CUDA_TRY(c->moments_fn(a, s));
-    if (stats) LBM_CUDA_TRY(launch_reduce(c->d_partials, c->nblocks, c->d_result, s));
+    int rc = launch_sample_moments(c, d_rho, d_u, residual, s);
+    if (rc) return rc;
     if (!dev && rho) LBM_CUDA_TRY(cudaMemcpyAsync(rho, d_rho, N * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (!dev && u) LBM_CUDA_TRY(cudaMemcpyAsync(u, d_u, d * N * sizeof(double), cudaMemcpyDeviceToHost, s));
-    int rc = LBM_OK;
     if (stats) {
-        double r[8];
-        LBM_CUDA_TRY(cudaMemcpyAsync(r, c->d_result, sizeof r, cudaMemcpyDeviceToHost, s));
+        std::vector<double> r(8 * c->samples.size());
+        LBM_CUDA_TRY(cudaMemcpyAsync(r.data(), c->d_result, r.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         LBM_CUDA_TRY(cudaStreamSynchronize(s));
-        stats->mass = r[0];
-        stats->momentum[0] = r[1];
-        stats->momentum[1] = r[2];
-        stats->momentum[2] = r[3];
-        stats->u2 = r[4];
-        stats->du2 = residual ? r[5] : 0.0;
-        stats->residual = residual && c->u_saved_valid && r[4] > 0 ? std::sqrt(r[5] / r[4]) : INFINITY;
-        stats->n_fluid = (int64_t)r[6];
-        stats->step = c->step;
+        double sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (size_t k = 0; k < c->samples.size(); k++)
+            for (int j = 0; j < 8; j++) sum[j] += r[8 * k + j];  // samples in order
+        fill_stats(c, sum, residual, c->u_saved_valid, stats);
         if (residual) c->u_saved_valid = true;
-        if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]) || !std::isfinite(r[3]))
-            rc = fail(LBM_ERR_DIVERGED, "mass or momentum is not finite at step %lld", (long long)c->step);
+        if (!finite_stats(*stats))
+            return fail(LBM_ERR_DIVERGED, "mass or momentum is not finite at step %lld", (long long)c->step);
     } else if (!dev && (rho || u)) {
         LBM_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    return rc;
+    return LBM_OK;
 }
 
-extern "C" int lbm_export_pdfs(lbm_ctx* c, double* pdfs, int flags, void* stream) {
-    if (!c || !pdfs) return fail(LBM_ERR_ARG, "NULL argument");
+extern "C" int lbm_moments_batch(lbm_ctx* c, lbm_stats* stats, int flags, void* stream) {
+    if (!c || !stats) return fail(LBM_ERR_ARG, "NULL argument");
     cudaStream_t s = S(stream);
-    const size_t n = (size_t)c->q * c->p.nx * c->p.ny * c->p.nz;
+    const bool residual = flags & LBM_STATS_RESIDUAL;
+    int rc = launch_sample_moments(c, nullptr, nullptr, residual, s);
+    if (rc) return rc;
+    std::vector<double> r(8 * c->samples.size());
+    LBM_CUDA_TRY(cudaMemcpyAsync(r.data(), c->d_result, r.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LBM_CUDA_TRY(cudaStreamSynchronize(s));
+    bool finite = true;
+    for (size_t k = 0; k < c->samples.size(); k++) {
+        fill_stats(c, &r[8 * k], residual, c->u_saved_valid, &stats[k]);
+        finite &= finite_stats(stats[k]);
+    }
+    if (residual) c->u_saved_valid = true;
+    if (!finite) return fail(LBM_ERR_DIVERGED, "a sample's mass or momentum is not finite at step %lld",
+                             (long long)c->step);
+    return LBM_OK;
+}
+
+extern "C" int lbm_export_pdfs_sample(lbm_ctx* c, int sample, double* pdfs, int flags, void* stream) {
+    if (!c || !pdfs) return fail(LBM_ERR_ARG, "NULL argument");
+    if (sample < 0 || sample >= (int)c->samples.size()) return fail(LBM_ERR_ARG, "no sample %d", sample);
+    cudaStream_t s = S(stream);
+    const SampleRange& r = c->samples[sample];
+    const size_t n = (size_t)c->q * r.nx * r.ny * r.nz;
     const bool dev = flags & LBM_OUT_DEVICE;
     double* d = pdfs;
     if (!dev) {
@@ -357,8 +459,7 @@ extern "C" int lbm_export_pdfs(lbm_ctx* c, double* pdfs, int flags, void* stream
         d = c->d_stage;
     }
     LBM_CUDA_TRY(launch_fill_nan(d, n, s));
-    NodeArgs a = c->na;
-    a.pdf = c->pdf[c->cur];
+    NodeArgs a = sample_args(c, sample);
     a.dense_pdf = d;
     LBM_CUDA_TRY(c->export_fn(a, s));
     if (!dev) {
@@ -368,8 +469,14 @@ extern "C" int lbm_export_pdfs(lbm_ctx* c, double* pdfs, int flags, void* stream
     return LBM_OK;
 }
 
+extern "C" int lbm_export_pdfs(lbm_ctx* c, double* pdfs, int flags, void* stream) {
+    if (c && c->samples.size() != 1) return fail(LBM_ERR_ARG, "a batch exports per sample (lbm_export_pdfs_sample)");
+    return lbm_export_pdfs_sample(c, 0, pdfs, flags, stream);
+}
+
 extern "C" int lbm_import_pdfs(lbm_ctx* c, const double* pdfs, int64_t step, int flags, void* stream) {
     if (!c || !pdfs) return fail(LBM_ERR_ARG, "NULL argument");
+    if (c->samples.size() != 1) return fail(LBM_ERR_ARG, "import needs a single-geometry context");
     cudaStream_t s = S(stream);
     const size_t n = (size_t)c->q * c->p.nx * c->p.ny * c->p.nz;
     const double* d = pdfs;
@@ -379,8 +486,7 @@ extern "C" int lbm_import_pdfs(lbm_ctx* c, const double* pdfs, int64_t step, int
         LBM_CUDA_TRY(cudaMemcpyAsync(c->d_stage, pdfs, n * sizeof(double), cudaMemcpyHostToDevice, s));
         d = c->d_stage;
     }
-    NodeArgs a = c->na;
-    a.pdf = c->pdf[c->cur];
+    NodeArgs a = sample_args(c, 0);
     a.dense_pdf_in = d;
     LBM_CUDA_TRY(c->import_fn(a, s));
     if (!(flags & LBM_OUT_DEVICE)) LBM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -388,6 +494,8 @@ extern "C" int lbm_import_pdfs(lbm_ctx* c, const double* pdfs, int64_t step, int
     c->u_saved_valid = false;
     return LBM_OK;
 }
+
+extern "C" int lbm_num_samples(const lbm_ctx* c) { return c ? (int)c->samples.size() : 0; }
 
 extern "C" int lbm_get_tiling(const lbm_ctx* c, lbm_tiling* out) {
     if (!c || !out) return fail(LBM_ERR_ARG, "NULL argument");

@@ -41,6 +41,14 @@ struct HostTiling {
     std::vector<uint32_t> nodes;             // fluid nodes, tile-major: tile * NT + node
     std::vector<WorkBlock> blocks;           // step-kernel blocks over `nodes`
 };
+// The tiles of one sample of a batch (a single geometry is a batch of one).
+struct SampleRange {
+    int nx, ny, nz;
+    int tile_begin, n_tiles;
+    long long n_fluid;
+};
+int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_t* const* masks, HostTiling* T,
+                       std::vector<SampleRange>* samples);
 int validate_params(const lbm_params* p);
 int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out);
 // Fluid-node list and step-kernel blocks of at most `threads` nodes and
@@ -69,6 +77,19 @@ struct FixedConsts {
     long long dws;        // sum_i w_i in Q60, minus 2^60 (exact)
 };
 
+// Constants of the float-float FP64 path: each a (hi, lo) pair of floats.
+struct FFConsts {
+    float2 w[3];       // w_c
+    float2 rho[3];     // w * w_c
+    float2 j[3];       // 3 w w_c
+    float2 keep;       // 1 - w
+    float2 alpha;      // 4.5 w
+    float2 g1;         // 1.5 w
+    float2 kf[3];      // 3 (1 - w/2) F_a
+    float2 beta[19];   // 9 (1 - w/2) (c_i.F)
+    float2 so[19];     // 3 (1 - w/2) w_i (c_i.F)
+};
+
 struct StepArgs {
     const WorkBlock* blocks;  // [n_work_blocks]
     const uint32_t* nodes;    // fluid-node list: tile * NT + node
@@ -88,6 +109,7 @@ struct StepArgs {
     float omega_f, force_f[3], f16_scale_f, f16_inv_scale_f;
     int* err;             // device error word (0 = none)
     FixedConsts fx;
+    FFConsts ffc;
 };
 
 struct NodeArgs {         // kernels that visit every node of every tile
@@ -98,7 +120,8 @@ struct NodeArgs {         // kernels that visit every node of every tile
     const int32_t* coords;
     const long long* tile_off;
     const int32_t* tile_stride;
-    int n_tiles;
+    int tile_begin;           // first tile of this launch (a sample of a batch)
+    int n_tiles;              // tiles of this launch
     int nx, ny, nz;
     double force[3];
     double rho0;
@@ -118,7 +141,7 @@ using StepLaunch = cudaError_t (*)(const StepArgs&, cudaStream_t);
 using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 
 // Kernel selection (nullptr when a combination is not compiled).
-StepLaunch select_step(int lattice, int a, int model, int storage, int arith);
+StepLaunch select_step(const lbm_params* p);
 NodeLaunch select_init(int lattice, int a, int model, int storage);
 NodeLaunch select_moments(int lattice, int a, int model, int storage);
 NodeLaunch select_export(int lattice, int a, int storage);
@@ -128,5 +151,6 @@ cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* result, cudaStream_t s);
 
 void fixed_consts(const lbm_params* p, FixedConsts* k);
+void ff_consts(const lbm_params* p, FFConsts* k);
 
 }  // namespace lbm

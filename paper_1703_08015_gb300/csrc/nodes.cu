@@ -30,9 +30,9 @@ template <class L, int A, int MODEL, class S>
 __global__ void k_init(const NodeArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
-    const int tile = blockIdx.x;
+    if ((int)blockIdx.x >= a.n_tiles) return;
+    const int tile = a.tile_begin + blockIdx.x;
     const int node = threadIdx.x;
-    if (tile >= a.n_tiles) return;
     const NodePos<A> p = node_pos<TL>(node);
     size_t n = 0;
     if (!own_fluid<TL>(a.tmask, tile, node) || !dense_index<L, A>(a, tile, p, n)) return;
@@ -65,9 +65,10 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
     __shared__ double red[NTH / 32][kStats];
     const int lt = threadIdx.x / TL::NT;
     const int node = threadIdx.x - lt * TL::NT;
-    const int tile = blockIdx.x * TPB + lt;
+    const int tile = a.tile_begin + blockIdx.x * TPB + lt;
+    const int tile_end = a.tile_begin + a.n_tiles;
     stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, a.tile_off, a.tile_stride,
-                                 static_cast<const unsigned char*>(a.pdf), (int)sizeof(T), a.n_tiles, tile, lt,
+                                 static_cast<const unsigned char*>(a.pdf), (int)sizeof(T), tile_end, tile, lt,
                                  node);
     __syncthreads();
     double acc[kStats];
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
     for (int k = 0; k < kStats; k++) acc[k] = 0.0;
     const NodePos<A> p = node_pos<TL>(node);
     size_t n = 0;
-    if (tile < a.n_tiles && mask_bit(sh, lt, TL::CENTER, node) && dense_index<L, A>(a, tile, p, n)) {
+    const bool want_fields = a.rho_out || a.u_out;
+    if (tile < tile_end && mask_bit(sh, lt, TL::CENTER, node) && (!want_fields || dense_index<L, A>(a, tile, p, n))) {
         T raw[L::Q];
         gather<L, A, TPB, T>(sh, lt, node, p, raw);
         double f[L::Q];
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
         double rho, jx, jy, jz, ux, uy, uz;
         moments_f64<L>(f, rho, jx, jy, jz);
         velocity_f64<L, MODEL>(rho, jx, jy, jz, a.force, ux, uy, uz);
-        const size_t N = (size_t)a.nx * a.ny * a.nz;
+        const size_t N = (size_t)a.nx * a.ny * a.nz;  // fields only for a single-sample launch
         if (a.rho_out) a.rho_out[n] = rho;
         if (a.u_out) {
             a.u_out[n] = ux;
@@ -152,8 +154,9 @@ template <class L, int A, class S>
 __global__ void k_export(const NodeArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
-    const int tile = blockIdx.x, node = threadIdx.x;
-    if (tile >= a.n_tiles || !own_fluid<TL>(a.tmask, tile, node)) return;
+    if ((int)blockIdx.x >= a.n_tiles) return;
+    const int tile = a.tile_begin + blockIdx.x, node = threadIdx.x;
+    if (!own_fluid<TL>(a.tmask, tile, node)) return;
     const NodePos<A> p = node_pos<TL>(node);
     size_t n;
     if (!dense_index<L, A>(a, tile, p, n)) return;
@@ -171,8 +174,9 @@ template <class L, int A, class S>
 __global__ void k_import(const NodeArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
-    const int tile = blockIdx.x, node = threadIdx.x;
-    if (tile >= a.n_tiles || !own_fluid<TL>(a.tmask, tile, node)) return;
+    if ((int)blockIdx.x >= a.n_tiles) return;
+    const int tile = a.tile_begin + blockIdx.x, node = threadIdx.x;
+    if (!own_fluid<TL>(a.tmask, tile, node)) return;
     const NodePos<A> p = node_pos<TL>(node);
     size_t n;
     if (!dense_index<L, A>(a, tile, p, n)) return;

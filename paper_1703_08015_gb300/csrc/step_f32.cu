@@ -92,61 +92,89 @@ __device__ __forceinline__ void collide_f32(float (&g)[L::Q], float omega, const
     });
 }
 
-template <class L, int A, int MODEL, class S>
-__global__ void __launch_bounds__(work_threads<L, A>()) k_step_f32(const StepArgs a) {
+template <class L, int A, int MODEL, class S, int BT, bool PERSIST>
+__global__ void __launch_bounds__(BT) k_step_f32(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
     using IO = F32Io<L, S>;
     __shared__ NeighShared<TL, work_tiles()> sh;
-    WorkNode wn;
-    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
-    const NodePos<A> p = node_pos<TL>(wn.node);
-    T raw[L::Q];
-    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
-    const int stride = sh.stride[wn.lt][TL::CENTER];
-    float g[L::Q];
-    static_for<0, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        g[i] = IO::template dev<i>(raw[i], a);
-    });
-    collide_f32<L, MODEL>(g, a.omega_f, a.force_f);
-    T* out = static_cast<T*>(a.dst) +
-             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
-    static_for<0, L::Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        out[i * stride] = IO::template raw<i>(g[i], a);
-    });
+    // one work block per thread block, or (persistent) a grid-stride loop over them
+    for (int wbi = blockIdx.x; wbi < a.n_work_blocks; wbi += PERSIST ? (int)gridDim.x : a.n_work_blocks) {
+        WorkNode wn;
+        if (stage_work_at<TL, work_tiles()>(sh, a, (int)sizeof(T), wbi, wn)) {
+            const NodePos<A> p = node_pos<TL>(wn.node);
+            T raw[L::Q];
+            const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
+            const int stride = sh.stride[wn.lt][TL::CENTER];
+            float g[L::Q];
+            static_for<0, L::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                g[i] = IO::template dev<i>(raw[i], a);
+            });
+            collide_f32<L, MODEL>(g, a.omega_f, a.force_f);
+            T* out = static_cast<T*>(a.dst) +
+                     (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+            static_for<0, L::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                out[i * stride] = IO::template raw<i>(g[i], a);
+            });
+        }
+        if (PERSIST) __syncthreads();  // the staging arrays are refilled for the next work block
+    }
 }
 
-template <class L, int A, int MODEL, class S>
+template <class L, int A, int MODEL, class S, int BT, bool PERSIST>
 cudaError_t launch_step_f32(const StepArgs& a, cudaStream_t s) {
     if (a.n_work_blocks == 0) return cudaSuccess;
-    k_step_f32<L, A, MODEL, S><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
+    int grid = a.n_work_blocks;
+    if (PERSIST) {
+        static int resident = 0;  // blocks of this kernel the GPU holds at once
+        if (!resident) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_f32<L, A, MODEL, S, BT, PERSIST>, BT, 0);
+            resident = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        grid = a.n_work_blocks < resident ? a.n_work_blocks : resident;
+    }
+    k_step_f32<L, A, MODEL, S, BT, PERSIST><<<grid, BT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
+template <class L, int A, int MODEL, class S>
+static StepLaunch pick_shape(int block_nodes, int persistent) {
+    constexpr int BD = work_threads<L, A>();
+    if constexpr (BD == 256) {
+        if (block_nodes == 128)
+            return persistent ? &launch_step_f32<L, A, MODEL, S, 128, true> : &launch_step_f32<L, A, MODEL, S, 128, false>;
+    }
+    if (block_nodes != 0 && block_nodes != BD) return nullptr;
+    return persistent ? &launch_step_f32<L, A, MODEL, S, BD, true> : &launch_step_f32<L, A, MODEL, S, BD, false>;
+}
+
 template <class L, int A, class S>
-static StepLaunch pick(int model) {
-    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_f32<L, A, LBM_QUASI_COMPRESSIBLE, S>
-                                           : &launch_step_f32<L, A, LBM_INCOMPRESSIBLE, S>;
+static StepLaunch pick(int model, int block_nodes, int persistent) {
+    return model == LBM_QUASI_COMPRESSIBLE ? pick_shape<L, A, LBM_QUASI_COMPRESSIBLE, S>(block_nodes, persistent)
+                                           : pick_shape<L, A, LBM_INCOMPRESSIBLE, S>(block_nodes, persistent);
 }
 
 template <class L, int A>
-static StepLaunch pick_storage(int model, int storage) {
-    if (storage == LBM_STORE_F32) return pick<L, A, StoreF32>(model);
-    if (storage == LBM_STORE_F16S) return pick<L, A, StoreF16S>(model);
-    if (storage == LBM_STORE_F32S) return pick<L, A, StoreF32S>(model);
+static StepLaunch pick_storage(int model, int storage, int block_nodes, int persistent) {
+    if (storage == LBM_STORE_F32) return pick<L, A, StoreF32>(model, block_nodes, persistent);
+    if (storage == LBM_STORE_F16S) return pick<L, A, StoreF16S>(model, block_nodes, persistent);
+    if (storage == LBM_STORE_F32S) return pick<L, A, StoreF32S>(model, block_nodes, persistent);
     return nullptr;
 }
 
-StepLaunch select_step_f32(int lattice, int a, int model, int storage) {
+StepLaunch select_step_f32(int lattice, int a, int model, int storage, int block_nodes, int persistent) {
     if (lattice == LBM_D2Q9) {
-        if (a == 8) return pick_storage<D2Q9, 8>(model, storage);
-        if (a == 16) return pick_storage<D2Q9, 16>(model, storage);
-        if (a == 32) return pick_storage<D2Q9, 32>(model, storage);
+        if (a == 8) return pick_storage<D2Q9, 8>(model, storage, block_nodes, persistent);
+        if (a == 16) return pick_storage<D2Q9, 16>(model, storage, block_nodes, persistent);
+        if (a == 32) return pick_storage<D2Q9, 32>(model, storage, block_nodes, persistent);
     } else if (lattice == LBM_D3Q19) {
-        if (a == 4) return pick_storage<D3Q19, 4>(model, storage);
-        if (a == 8) return pick_storage<D3Q19, 8>(model, storage);
+        if (a == 4) return pick_storage<D3Q19, 4>(model, storage, block_nodes, persistent);
+        if (a == 8) return pick_storage<D3Q19, 8>(model, storage, block_nodes, persistent);
     }
     return nullptr;
 }

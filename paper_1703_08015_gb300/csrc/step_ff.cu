@@ -1,0 +1,343 @@
+// step_ff.cu -- the FP64 tiled step with float-float arithmetic.
+//
+// Same update as step_fixed.cu (Eq. 7 with Eq. 2, Eq. 3/4, Eq. 5/6 and Guo
+// forcing, written on deviations g_i = f_i - w_i), but every product is
+// evaluated on pairs of FP32 numbers (hi + lo, ~48 significant bits) with
+// fused multiply-adds, which GB300 issues at its full FP32 rate, instead of
+// 64x64-bit integer multiplies.
+//
+//   * g_i comes from the FP64 bit patterns exactly: d_i = bits(f_i) - bits(w_i)
+//     is an integer when f_i shares the binade of w_i, and two 24-bit halves of
+//     d_i convert to FP32 exactly when |d_i| < 2^47;
+//   * rho - 1 and j are exact 64-bit integer sums (units of 2^-60), converted
+//     to float-float once per node;
+//   * every f*_i is rounded once to FP64 (faithfully: within one unit of the
+//     last place of the exact float-float result).
+// Nodes outside that range (|f_i - w_i| beyond ~w_i/32, |j| >= 1/16,
+// |rho - 1| >= 1/32, NaN, negative values) are recomputed in native FP64.
+#include <cmath>
+#include <cstdlib>
+
+#include "collide_f64.cuh"
+#include "tile.cuh"
+
+namespace lbm {
+
+struct ff {
+    float h, l;
+};
+
+// s + e = a + b exactly, for |a| >= |b| (or a = 0).
+__device__ __forceinline__ ff fast2(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// Sums are renormalised (after cancellation the low part could otherwise
+// grow to the size of the high part, and a following product would evaluate
+// it in single precision); products return (p, e) with |e| within a few ulps
+// of p, which every consumer accepts, saving a two-sum per product.
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const ff s = two_sum(x.h, y.h);
+    return fast2(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.h, -x.l}; }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return ff{p, e};
+}
+
+__device__ __forceinline__ ff ff_sqr(ff x) {
+    const float p = __fmul_rn(x.h, x.h);
+    float e = __fmaf_rn(x.h, x.h, -p);
+    e = __fmaf_rn(__fmul_rn(2.f, x.h), x.l, e);
+    return ff{p, e};
+}
+
+__device__ __forceinline__ ff ff_c(const float2 k) { return ff{k.x, k.y}; }
+
+constexpr float pow2f(int e) {
+    float v = 1.f;
+    while (e > 0) {
+        v *= 2.f;
+        e--;
+    }
+    while (e < 0) {
+        v *= 0.5f;
+        e++;
+    }
+    return v;
+}
+
+constexpr int fp_exp(double w) {
+    int e = 0;
+    while (w < 1.0) {
+        w *= 2.0;
+        e--;
+    }
+    while (w >= 2.0) {
+        w *= 0.5;
+        e++;
+    }
+    return e;
+}
+
+template <class L, int I>
+struct FFLink {
+    using K = Link<L, I>;
+    static constexpr int E = fp_exp(K::w);  // binade of w_i: ulp(w_i) = 2^(E - 52)
+    static constexpr int SHIFT = E + 8;     // d << SHIFT is g in units of 2^-60
+    static constexpr float HI = pow2f(E - 28), LO = pow2f(E - 52), TO_ULP = pow2f(52 - E);
+    static constexpr int REP = I < K::opp ? I : K::opp;
+};
+
+__device__ __forceinline__ bool small_ll(long long x, int log2bound) {
+    return (unsigned long long)(x + (1ll << log2bound)) < (2ull << log2bound);
+}
+
+// A value x * 2^-60 (|x| < 2^57) as float-float, exactly up to the last piece.
+__device__ __forceinline__ ff q60_to_ff(long long x) {
+    const float f2 = __fmul_rn(__int2float_rn((int)(x >> 48)), pow2f(-12));
+    const float f1 = __fmul_rn(__int2float_rn((int)((x >> 24) & 0xFFFFFF)), pow2f(-36));
+    const float f0 = __fmul_rn(__int2float_rn((int)(x & 0xFFFFFF)), pow2f(-60));
+    const ff s = fast2(f2, f1);
+    return fast2(s.h, __fadd_rn(s.l, f0));
+}
+
+// FP64 bit pattern of w + x * 2^(E-52), x given as float-float in units of
+// ulp(w) (|x| < 2^48); the integer is taken within one unit of the exact x.
+__device__ __forceinline__ unsigned long long ulp_to_bits(ff x, unsigned long long wb, bool& ok) {
+    const float rh = rintf(x.h);
+    const float t = __fadd_rn(__fsub_rn(x.h, rh), x.l);
+    const int k = __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;  // rint(t), |t| < 2^22
+    const unsigned bits = __float_as_uint(rh);
+    const int e = (int)((bits >> 23) & 0xFF);
+    const unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u) << 24;
+    ok &= e <= 174;  // |rh| < 2^48
+    const unsigned long long mag = (e >= 127 && e <= 174) ? m >> (174 - e) : 0ull;
+    const long long v = (bits >> 31) ? -(long long)mag : (long long)mag;
+    const unsigned long long out = wb + (unsigned long long)(v + k);
+    ok &= ((out ^ wb) >> 52) == 0;
+    return out;
+}
+
+template <class L, int C>
+constexpr int ff_first_of_class() {
+    int i = 0;
+    while (i < L::Q && L::cls_[i] != C) i++;
+    return i;
+}
+
+template <class L, int MODEL>
+__device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], const FixedConsts& k,
+                                           const FFConsts& c, unsigned long long* out, int stride) {
+    constexpr int Q = L::Q;
+    long long d[Q];
+    bool ok = true;
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        d[i] = (long long)(b[i] - (unsigned long long)k.w_bits[Link<L, i>::cls]);
+        ok &= small_ll(d[i], 47);  // also rejects another binade, sign, NaN/Inf
+    });
+    long long dr = k.dws, jx = k.half_f[0], jy = k.half_f[1], jz = k.half_f[2];
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using K = Link<L, i>;
+        const long long g = d[i] << FFLink<L, i>::SHIFT;
+        dr += g;
+        if constexpr (K::cx > 0) jx += g;
+        if constexpr (K::cx < 0) jx -= g;
+        if constexpr (K::cy > 0) jy += g;
+        if constexpr (K::cy < 0) jy -= g;
+        if constexpr (K::cz > 0) jz += g;
+        if constexpr (K::cz < 0) jz -= g;
+    });
+    ok &= small_ll(dr, 55) & small_ll(jx, 56) & small_ll(jy, 56) & small_ll(jz, 56);
+    if (!ok) return false;
+
+    const ff DR = q60_to_ff(dr), JX = q60_to_ff(jx), JY = q60_to_ff(jy);
+    const ff JZ = L::D == 3 ? q60_to_ff(jz) : ff{0.f, 0.f};
+    ff RINV{1.f, 0.f};  // 1 / rho
+    if constexpr (MODEL == LBM_QUASI_COMPRESSIBLE) {
+        ff rho = fast2(1.f, DR.h);
+        rho = fast2(rho.h, __fadd_rn(rho.l, DR.l));
+        const float r0 = __frcp_rn(rho.h);
+        // r = r0 + r0 (1 - rho r0), with 1 - rho r0 formed exactly enough
+        const float p = __fmul_rn(rho.h, r0);
+        const float pe = __fmaf_rn(rho.h, r0, -p);
+        const float er = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(rho.l, r0));
+        RINV = fast2(r0, __fmul_rn(r0, er));
+    }
+    const ff jj = ff_add(ff_add(ff_sqr(JX), ff_sqr(JY)), ff_sqr(JZ));
+    const ff gamma = ff_add(ff_mul(jj, ff_c(c.g1)),
+                            ff_add(ff_add(ff_mul(JX, ff_c(c.kf[0])), ff_mul(JY, ff_c(c.kf[1]))),
+                                   ff_mul(JZ, ff_c(c.kf[2]))));
+    auto emit = [&](auto I, ff s) {
+        constexpr int i = decltype(I)::value;
+        constexpr float sc = FFLink<L, i>::TO_ULP;
+        const ff x{__fmul_rn(s.h, sc), __fmul_rn(s.l, sc)};
+        out[i * stride] = ulp_to_bits(x, (unsigned long long)k.w_bits[Link<L, i>::cls], ok);
+    };
+    auto link_ff = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using F = FFLink<L, i>;
+        return ff{__fmul_rn(__int2float_rn((int)(d[i] >> 24)), F::HI),
+                  __fmul_rn(__int2float_rn((int)(d[i] & 0xFFFFFF)), F::LO)};
+    };
+    const ff KEEP = ff_c(c.keep);
+    ff R{0.f, 0.f}, V{0.f, 0.f}, PX{0.f, 0.f}, PY{0.f, 0.f}, PZ{0.f, 0.f};
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using F = FFLink<L, i>;
+        using K = Link<L, i>;
+        if constexpr (F::REP == i) {
+            constexpr int cl = K::cls;
+            if constexpr (i == ff_first_of_class<L, cl>()) {
+                R = ff_mul(DR, ff_c(c.rho[cl]));
+                V = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[cl])) : ff_c(c.w[cl]);
+                if constexpr (cl > 0) {
+                    PX = ff_mul(JX, ff_c(c.j[cl]));
+                    PY = ff_mul(JY, ff_c(c.j[cl]));
+                    if constexpr (L::D == 3) PZ = ff_mul(JZ, ff_c(c.j[cl]));
+                }
+            }
+            if constexpr (i == 0) {
+                emit(I, ff_add(ff_mul(link_ff(I), KEEP), ff_add(R, ff_mul(ff_neg(gamma), V))));
+            } else {
+                constexpr int j = K::opp;
+                ff Y{0.f, 0.f}, O = ff_c(c.so[i]);
+                auto acc = [&](int sgn, const ff& JA, const ff& PA) {
+                    Y = ff_add(Y, sgn > 0 ? JA : ff_neg(JA));
+                    O = ff_add(O, sgn > 0 ? PA : ff_neg(PA));
+                };
+                if constexpr (K::cx != 0) acc(K::cx, JX, PX);
+                if constexpr (K::cy != 0) acc(K::cy, JY, PY);
+                if constexpr (K::cz != 0) acc(K::cz, JZ, PZ);
+                const ff A = ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[i]));
+                const ff T = ff_mul(Y, A);
+                const ff E = ff_add(R, ff_mul(ff_add(T, ff_neg(gamma)), V));
+                emit(I, ff_add(ff_add(ff_mul(link_ff(I), KEEP), E), O));
+                emit(std::integral_constant<int, j>{},
+                     ff_add(ff_add(ff_mul(link_ff(std::integral_constant<int, j>{}), KEEP), E), ff_neg(O)));
+            }
+        }
+    });
+    return ok;
+}
+
+template <class L, int A, int MODEL, int MINB>
+__global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const StepArgs a) {
+    using TL = Tile<L, A>;
+    using T = unsigned long long;
+    __shared__ NeighShared<TL, work_tiles()> sh;
+    WorkNode wn;
+    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    const NodePos<A> p = node_pos<TL>(wn.node);
+    T b[L::Q];
+    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
+    const int stride = sh.stride[wn.lt][TL::CENTER];
+    T* out = static_cast<T*>(a.dst) +
+             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+    if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
+        // out of range: the same update with FP64 instructions
+        gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
+        double f[L::Q];
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[i] = __longlong_as_double((long long)b[i]);
+        });
+        collide_f64<L, MODEL>(f, a.omega, a.force);
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            out[i * stride] = (T)__double_as_longlong(f[i]);
+        });
+    }
+}
+
+template <class L, int A, int MODEL, int MINB>
+cudaError_t launch_step_ff(const StepArgs& a, cudaStream_t s) {
+    if (a.n_work_blocks == 0) return cudaSuccess;
+    k_step_ff<L, A, MODEL, MINB><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- host: float-float constants ------------------------------------------------
+static float2 split(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+template <class L>
+static void ff_consts_for(const lbm_params* p, FFConsts* k) {
+    const double omega = 1.0 / p->tau;
+    const double kf = 1.0 - 0.5 * omega;
+    const double F[3] = {p->force[0], p->force[1], L::D == 3 ? p->force[2] : 0.0};
+    for (int c = 0; c < 3; c++) {
+        const double w = L::wc_[c];
+        k->w[c] = split(w);
+        k->rho[c] = split(omega * w);
+        k->j[c] = split(3.0 * omega * w);
+    }
+    k->keep = split(1.0 - omega);
+    k->alpha = split(4.5 * omega);
+    k->g1 = split(1.5 * omega);
+    for (int a = 0; a < 3; a++) k->kf[a] = split(3.0 * kf * F[a]);
+    for (int i = 0; i < L::Q; i++) {
+        const double cF = L::cx_[i] * F[0] + L::cy_[i] * F[1] + L::cz_[i] * F[2];
+        k->beta[i] = split(9.0 * kf * cF);
+        k->so[i] = split(3.0 * kf * L::wc_[L::cls_[i]] * cF);
+    }
+}
+
+void ff_consts(const lbm_params* p, FFConsts* k) {
+    *k = FFConsts{};
+    if (p->lattice == LBM_D2Q9)
+        ff_consts_for<D2Q9>(p, k);
+    else if (p->lattice == LBM_D3Q19)
+        ff_consts_for<D3Q19>(p, k);
+}
+
+template <class L, int A, int MODEL>
+static StepLaunch pick_minb(int minb) {
+    switch (minb) {
+        case 1: return &launch_step_ff<L, A, MODEL, 1>;
+        case 2: return &launch_step_ff<L, A, MODEL, 2>;
+        default: return &launch_step_ff<L, A, MODEL, 3>;
+    }
+}
+
+template <class L, int A>
+static StepLaunch pick(int model, int minb) {
+    return model == LBM_QUASI_COMPRESSIBLE ? pick_minb<L, A, LBM_QUASI_COMPRESSIBLE>(minb)
+                                           : pick_minb<L, A, LBM_INCOMPRESSIBLE>(minb);
+}
+
+// Resident blocks per SM the compiler is asked to allow: LBM_FF_MINBLOCKS.
+StepLaunch select_step_ff(int lattice, int a, int model) {
+    const char* v = std::getenv("LBM_FF_MINBLOCKS");
+    int minb = v ? std::atoi(v) : 3;
+    if (minb < 1 || minb > 3) minb = 3;
+    if (lattice == LBM_D2Q9) {
+        if (a == 8) return pick<D2Q9, 8>(model, minb);
+        if (a == 16) return pick<D2Q9, 16>(model, minb);
+        if (a == 32) return pick<D2Q9, 32>(model, minb);
+    } else if (lattice == LBM_D3Q19) {
+        if (a == 4) return pick<D3Q19, 4>(model, minb);
+        if (a == 8) return pick<D3Q19, 8>(model, minb);
+    }
+    return nullptr;
+}
+
+}  // namespace lbm

@@ -190,9 +190,9 @@ struct WorkNode {
 // fluid node.  Every thread of the block must call it (it holds the barrier);
 // returns false for threads beyond the block's node count.
 template <class TL, int KMAX>
-__device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
-                                           WorkNode& wn) {
-    const WorkBlock wb = a.blocks[blockIdx.x];
+__device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
+                                              int wbi, WorkNode& wn) {
+    const WorkBlock wb = a.blocks[wbi];
     const unsigned char* pdf = static_cast<const unsigned char*>(a.src);
     for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
         const int lt = k / (TL::NN * TL::W);
@@ -212,6 +212,12 @@ __device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const Step
     wn.node = (int)(e & (TL::NT - 1));
     wn.lt = wn.tile - wb.tile_begin;
     return true;
+}
+
+template <class TL, int KMAX>
+__device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
+                                           WorkNode& wn) {
+    return stage_work_at<TL, KMAX>(sh, a, value_bytes, blockIdx.x, wn);
 }
 
 }  // namespace lbm

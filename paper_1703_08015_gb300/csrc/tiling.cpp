@@ -185,6 +185,59 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     return LBM_OK;
 }
 
+// Several geometries in one tiling: each sample is tiled on its own and its
+// tables are appended, with its tile indices (in the neighbour records) and
+// its PDF offsets shifted past the samples before it.  The step kernels then
+// treat the batch as one sparse geometry whose pieces never touch.
+int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_t* const* masks, HostTiling* T,
+                       std::vector<SampleRange>* samples) {
+    if (!p || n < 1 || !dims || !masks) return fail(LBM_ERR_ARG, "batch: bad arguments");
+    *T = HostTiling{};
+    samples->clear();
+    long long total_tiles = 0, total_values = 0, total_mesh = 0, total_fluid = 0;
+    size_t total_bytes = 0;
+    for (int k = 0; k < n; k++) {
+        lbm_params ps = *p;
+        ps.nx = dims[3 * k];
+        ps.ny = dims[3 * k + 1];
+        ps.nz = dims[3 * k + 2];
+        HostTiling S;
+        int rc = build_tiling(&ps, masks[k], &S);
+        if (rc) {
+            char msg[400];
+            snprintf(msg, sizeof msg, "%s", g_err);
+            return fail(rc, "batch sample %d: %s", k, msg);
+        }
+        if (total_tiles + S.info.n_ftiles > INT32_MAX) return fail(LBM_ERR_CAPACITY, "batch: too many tiles");
+        const int base_t = (int)total_tiles;
+        T->a = S.a;
+        T->d = S.d;
+        T->nn = S.nn;
+        T->words = S.words;
+        T->tmask.insert(T->tmask.end(), S.tmask.begin(), S.tmask.end());
+        T->coords.insert(T->coords.end(), S.coords.begin(), S.coords.end());
+        for (int32_t v : S.nbr) T->nbr.push_back(v >= 0 ? v + base_t : -1);
+        for (long long o : S.tile_off) T->tile_off.push_back(o + total_values);
+        T->tile_stride.insert(T->tile_stride.end(), S.tile_stride.begin(), S.tile_stride.end());
+        samples->push_back(SampleRange{ps.nx, ps.ny, ps.nz, base_t, S.info.n_ftiles, S.info.n_fluid});
+        total_tiles += S.info.n_ftiles;
+        total_mesh += S.info.n_tiles;
+        total_fluid += S.info.n_fluid;
+        total_bytes += S.info.pdf_bytes;
+        total_values += (long long)(S.info.pdf_bytes / bytes_per_value(p->storage));
+    }
+    const int nt = T->d == 3 ? T->a * T->a * T->a : T->a * T->a;
+    if (total_tiles * nt > (long long)UINT32_MAX) return fail(LBM_ERR_CAPACITY, "batch: too many tile slots");
+    lbm_tiling& I = T->info;
+    I.ntx = I.nty = I.ntz = 0;
+    I.n_tiles = (int32_t)(total_mesh > INT32_MAX ? INT32_MAX : total_mesh);
+    I.n_ftiles = (int32_t)total_tiles;
+    I.nbr_per_tile = T->nn;
+    I.n_fluid = total_fluid;
+    I.pdf_bytes = total_bytes;
+    return LBM_OK;
+}
+
 int work_threads_for(int lattice, int a) {
     const int nt = lattice == LBM_D2Q9 ? a * a : a * a * a;
     return nt > 256 ? nt : 256;
@@ -231,6 +284,18 @@ extern "C" int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask, int32
     *out = T.info;
     if (tile_map) std::memcpy(tile_map, T.tile_map.data(), T.tile_map.size() * sizeof(int32_t));
     if (nbr) std::memcpy(nbr, T.nbr.data(), T.nbr.size() * sizeof(int32_t));
+    return LBM_OK;
+}
+
+extern "C" int lbm_build_tilemap_batch(const lbm_params* p, int n_samples, const int* dims,
+                                       const uint8_t* const* masks, lbm_tiling* out) {
+    using namespace lbm;
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    HostTiling T;
+    std::vector<SampleRange> samples;
+    int rc = build_batch_tiling(p, n_samples, dims, masks, &T, &samples);
+    if (rc) return rc;
+    *out = T.info;
     return LBM_OK;
 }
 

@@ -248,3 +248,22 @@ def workload(name: str, seed: int = None):
     else:
         raise KeyError(name)
     return mask, params, info
+
+
+def batch_workload(n: int = 64, seed: int = 5, side_min: int = 32, side_max: int = 160,
+                   phi_min: float = 0.1, phi_max: float = 0.6):
+    """Independent porous samples of uneven size and sparsity: cube sides
+    drawn uniformly from the multiples of 8 in [side_min, side_max] (so that
+    4^3 and 8^3 tiles divide the periodic x axis), fluid fractions uniform in
+    [phi_min, phi_max], overlapping sphere packs (radius 4-12) with their own
+    seeds.  Returns (masks, info list)."""
+    rng = _rng(seed)
+    sides = np.arange(side_min, side_max + 1, 8)
+    masks, infos = [], []
+    for k in range(n):
+        side = int(rng.choice(sides))
+        phi = float(rng.uniform(phi_min, phi_max))
+        m, info = sphere_pack_3d(side, seed=seed * 1000 + k, target_fluid=phi)
+        masks.append(m)
+        infos.append({"side": side, "target_fluid": phi, **info})
+    return masks, infos

@@ -21,11 +21,13 @@ ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_SHAPE", -3: "LBM_ERR_CUDA", -4: "LBM_E
 LBM_D2Q9, LBM_D3Q19 = 9, 19
 LBM_QUASI_COMPRESSIBLE, LBM_INCOMPRESSIBLE = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S, LBM_STORE_F32S = 0, 1, 2, 3
-LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED = 0, 1, 2
+LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED, LBM_ARITH_FF = 0, 1, 2, 3
 LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
 
 EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
-            "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc")
+            "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc",
+            "lbm_build_tilemap_batch", "lbm_init_batch", "lbm_moments_batch", "lbm_export_pdfs_sample",
+            "lbm_num_samples")
 LBM_NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -40,7 +42,8 @@ class lbm_params(ctypes.Structure):
                 ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("tile_a", ctypes.c_int),
                 ("periodic", ctypes.c_int * 3), ("tau", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("storage", ctypes.c_int),
-                ("arith", ctypes.c_int), ("f16_scale", ctypes.c_double)]
+                ("arith", ctypes.c_int), ("f16_scale", ctypes.c_double),
+                ("block_nodes", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class lbm_tiling(ctypes.Structure):
@@ -80,6 +83,12 @@ def library(build: bool = True):
             lib.lbm_get_tiling.argtypes = [P, ctypes.POINTER(lbm_tiling)]
             lib.lbm_free.argtypes = [P]
             lib.lbm_stats_noalloc.argtypes = [P, P, P]
+            lib.lbm_build_tilemap_batch.argtypes = [ctypes.POINTER(lbm_params), I, P, P, ctypes.POINTER(lbm_tiling)]
+            lib.lbm_init_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(lbm_params), I, P, P, P, P,
+                                           ctypes.c_size_t, P]
+            lib.lbm_moments_batch.argtypes = [P, P, I, P]
+            lib.lbm_export_pdfs_sample.argtypes = [P, I, P, I, P]
+            lib.lbm_num_samples.argtypes = [P]
             lib.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
                 getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -108,7 +117,7 @@ def lbm_last_error() -> str:
 
 def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0, 0.0, 0.0),
                 rho0=1.0, model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64,
-                arith=LBM_ARITH_AUTO, f16_scale=0.0) -> lbm_params:
+                arith=LBM_ARITH_AUTO, f16_scale=0.0, block_nodes=0, persistent=0) -> lbm_params:
     """lbm_params from a mask shape (nz, ny, nx) or (ny, nx)."""
     if len(shape) == 2:
         shape = (1,) + tuple(shape)
@@ -119,6 +128,7 @@ def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0,
         p.periodic[k] = int(bool(periodic[k])) if k < len(periodic) else 0
         p.force[k] = float(force[k]) if k < len(force) else 0.0
     p.tau, p.rho0, p.storage, p.arith, p.f16_scale = float(tau), float(rho0), storage, arith, float(f16_scale)
+    p.block_nodes, p.persistent = int(block_nodes), int(persistent)
     return p
 
 
@@ -181,8 +191,90 @@ def lbm_stats_noalloc(ctx, stats_dev, stream=None):
     return _check(library().lbm_stats_noalloc(ctx, _ptr(stats_dev), stream))
 
 
+def _batch_args(masks):
+    ms = [np.ascontiguousarray(m[None] if m.ndim == 2 else m, np.uint8) for m in masks]
+    dims = np.array([[m.shape[2], m.shape[1], m.shape[0]] for m in ms], np.int32)
+    ptrs = (ctypes.c_void_p * len(ms))(*[m.ctypes.data for m in ms])
+    return ms, dims, ptrs
+
+
+def lbm_build_tilemap_batch(params: lbm_params, masks) -> lbm_tiling:
+    ms, dims, ptrs = _batch_args(masks)
+    info = lbm_tiling()
+    _check(library().lbm_build_tilemap_batch(ctypes.byref(params), len(ms), _ptr(dims), ptrs,
+                                             ctypes.byref(info)))
+    return info
+
+
+def lbm_init_batch(params: lbm_params, masks, pdf_a, pdf_b, pdf_bytes, stream=None):
+    ms, dims, ptrs = _batch_args(masks)
+    ctx = ctypes.c_void_p()
+    _check(library().lbm_init_batch(ctypes.byref(ctx), ctypes.byref(params), len(ms), _ptr(dims), ptrs,
+                                    _ptr(pdf_a), _ptr(pdf_b), pdf_bytes, stream))
+    return ctx
+
+
+def lbm_moments_batch(ctx, n_samples, flags=0, stream=None):
+    """Per-sample lbm_stats (list); LBM_ERR_DIVERGED is returned, not raised."""
+    arr = (lbm_stats * n_samples)()
+    rc = library().lbm_moments_batch(ctx, ctypes.cast(arr, ctypes.c_void_p), int(flags), stream)
+    if rc not in (LBM_OK, -5):
+        _check(rc)
+    return list(arr), rc
+
+
+def lbm_export_pdfs_sample(ctx, sample, out, flags=0, stream=None):
+    return _check(library().lbm_export_pdfs_sample(ctx, int(sample), _ptr(out), int(flags), stream))
+
+
 def lbm_free(ctx):
     return _check(library().lbm_free(ctx))
+
+
+class BatchSolver:
+    """A batch context (many geometries, one concatenated tile list) plus its
+    two PDF copies held as PyTorch device tensors."""
+
+    def __init__(self, masks, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
+                 model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F32S, arith=LBM_ARITH_AUTO,
+                 f16_scale=0.0, block_nodes=0, persistent=0, device="cuda"):
+        import torch
+
+        self.masks = [np.ascontiguousarray(m[None] if m.ndim == 2 else m, np.uint8) for m in masks]
+        self.q = lattice
+        self.params = make_params(lattice, self.masks[0].shape, tile_a, periodic, tau, force, rho0, model,
+                                  storage, arith, f16_scale, block_nodes, persistent)
+        self.tiling = lbm_build_tilemap_batch(self.params, self.masks)
+        nbytes = max(int(self.tiling.pdf_bytes), 256)
+        self.device = torch.device(device)
+        self.pdf = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.stream = torch.cuda.current_stream(self.device)
+        self.ctx = lbm_init_batch(self.params, self.masks, self.pdf[0], self.pdf[1], nbytes, self._s())
+
+    def _s(self):
+        return ctypes.c_void_p(self.stream.cuda_stream)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n, self._s())
+
+    def stats(self, residual=False):
+        return lbm_moments_batch(self.ctx, len(self.masks), LBM_STATS_RESIDUAL if residual else 0, self._s())
+
+    def export_pdfs(self, k):
+        out = np.empty((self.q,) + self.masks[k].shape, np.float64)
+        lbm_export_pdfs_sample(self.ctx, k, out, 0, self._s())
+        return out
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
@@ -190,7 +282,7 @@ class Solver:
 
     def __init__(self, mask, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
                  model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64, arith=LBM_ARITH_AUTO,
-                 f16_scale=0.0, rho_init=None, u_init=None, device="cuda"):
+                 f16_scale=0.0, rho_init=None, u_init=None, block_nodes=0, persistent=0, device="cuda"):
         import torch
 
         self.torch = torch
@@ -201,7 +293,7 @@ class Solver:
         self.shape = self.mask.shape
         self.q = lattice
         self.params = make_params(lattice, self.shape, tile_a, periodic, tau, force, rho0, model, storage,
-                                  arith, f16_scale)
+                                  arith, f16_scale, block_nodes, persistent)
         self.tiling, _, _ = lbm_build_tilemap(self.params, self.mask, want_map=False, want_nbr=False)
         nbytes = max(int(self.tiling.pdf_bytes), 256)
         self.device = torch.device(device)

@@ -99,3 +99,20 @@ def test_null_arguments_are_rejected():
     assert lib.lbm_moments(None, None, None, None, 0, None) == -1
     assert lib.lbm_free(None) == 0
     assert "NULL" in lbm.lbm_last_error() or lbm.lbm_last_error() != ""
+
+
+def test_batch_tiling_sums_the_samples():
+    masks = [geo.random_mask(8 * (k + 1), 12, 6 + k, fluid=0.4, seed=k) for k in range(4)]
+    p = lbm.make_params(lbm.LBM_D3Q19, (1, 1, 1), 4, (1, 0, 0))
+    total = lbm.lbm_build_tilemap_batch(p, masks)
+    n_ftiles = pdf = fluid = 0
+    for m in masks:
+        info, _, _ = lbm.lbm_build_tilemap(lbm.make_params(lbm.LBM_D3Q19, m.shape, 4, (1, 0, 0)), m, False, False)
+        n_ftiles += info.n_ftiles
+        pdf += info.pdf_bytes
+        fluid += info.n_fluid
+    assert (total.n_ftiles, total.pdf_bytes, total.n_fluid) == (n_ftiles, pdf, fluid)
+    bad = [masks[0], geo.random_mask(10, 12, 6, seed=9)]  # nx = 10 not a multiple of 4 on periodic x
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_build_tilemap_batch(p, bad)
+    assert e.value.code == -2

@@ -43,7 +43,7 @@ def run_both(oracle, mask, lattice, a, per, tau, F, steps, model=0, arith=lbm.LB
     return gpu, ref
 
 
-ARITHS = [lbm.LBM_ARITH_F64, lbm.LBM_ARITH_FIXED]
+ARITHS = [lbm.LBM_ARITH_F64, lbm.LBM_ARITH_FIXED, lbm.LBM_ARITH_FF]
 
 
 def _small_cases():
@@ -62,7 +62,7 @@ def _small_cases():
     ]
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
 @pytest.mark.parametrize("case", _small_cases(), ids=lambda c: c[0])
 def test_parity_small(oracle, case, arith):
     name, mask, lattice, a, per, tau, F, steps, model = case
@@ -71,7 +71,7 @@ def test_parity_small(oracle, case, arith):
     assert err <= TOL, (name, err)
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
 def test_parity_d2q9_circles_128_full(oracle, arith):
     """128^2 circles, 16^2 tiles, tau 0.8, F = 1e-6, 1000 steps, every node."""
     mask, params, _ = geo.workload("d2q9_circles_128")
@@ -80,7 +80,7 @@ def test_parity_d2q9_circles_128_full(oracle, arith):
     assert max_rel(gpu, ref, mask) <= TOL
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
 def test_parity_d3q19_spheres_64_2000_steps(oracle, arith):
     """A 64^3 piece of the sphere-pack workload at its full step count."""
     mask, _ = geo.sphere_pack_3d(64, seed=21)
@@ -119,7 +119,7 @@ def test_full_size_sampled_step_and_mass(oracle, name):
     assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-13
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
 def test_moments_and_stats(oracle, arith):
     _cuda()
     mask, _ = geo.sphere_pack_3d(shape=(20, 17, 15), seed=5, r_min=2, r_max=4, target_fluid=0.5)
@@ -166,7 +166,7 @@ def test_checkpoint_resume_is_bit_exact():
     assert st.step == 150
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
 def test_edge_cases(oracle, arith):
     _cuda()
     # all solid: nothing to do, nothing to sum
