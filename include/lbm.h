@@ -267,6 +267,11 @@ int lbm_init_batch(lbm_ctx** out, const lbm_params* p, int n_samples, const int*
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_DIVERGED (some sample). */
 int lbm_moments_batch(lbm_ctx* ctx, lbm_stats* stats, int flags, void* stream);
 
+/* The rho / u fields of lbm_moments for sample k of a batch (dense over that
+ * sample's box, NaN at solid nodes; host or device with LBM_OUT_DEVICE).
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_moments_sample(lbm_ctx* ctx, int sample, double* rho, double* u, int flags, void* stream);
+
 /* lbm_export_pdfs for sample k of a batch (dense over that sample's box).
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_export_pdfs_sample(lbm_ctx* ctx, int sample, double* pdfs, int flags, void* stream);

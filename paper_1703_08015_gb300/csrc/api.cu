@@ -425,6 +425,37 @@ extern "C" int lbm_moments(lbm_ctx* c, double* rho, double* u, lbm_stats* stats,
     return LBM_OK;
 }
 
+extern "C" int lbm_moments_sample(lbm_ctx* c, int sample, double* rho, double* u, int flags, void* stream) {
+    if (!c || (!rho && !u)) return fail(LBM_ERR_ARG, "NULL argument");
+    if (sample < 0 || sample >= (int)c->samples.size()) return fail(LBM_ERR_ARG, "no sample %d", sample);
+    cudaStream_t s = S(stream);
+    const SampleRange& r = c->samples[sample];
+    const size_t N = (size_t)r.nx * r.ny * r.nz;
+    const int d = c->p.lattice == LBM_D3Q19 ? 3 : 2;
+    const bool dev = flags & LBM_OUT_DEVICE;
+    double* d_rho = rho;
+    double* d_u = u;
+    if (!dev) {
+        int rc = ensure_stage(c, N * (1 + d) * sizeof(double));
+        if (rc) return rc;
+        d_rho = rho ? c->d_stage : nullptr;
+        d_u = u ? c->d_stage + N : nullptr;
+    }
+    if (d_rho) LBM_CUDA_TRY(launch_fill_nan(d_rho, N, s));
+    if (d_u) LBM_CUDA_TRY(launch_fill_nan(d_u, d * N, s));
+    NodeArgs a = sample_args(c, sample);
+    a.rho_out = d_rho;
+    a.u_out = d_u;
+    a.partials = c->d_partials + (size_t)8 * c->part_begin[sample];
+    LBM_CUDA_TRY(c->moments_fn(a, s));
+    if (!dev) {
+        if (rho) LBM_CUDA_TRY(cudaMemcpyAsync(rho, d_rho, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (u) LBM_CUDA_TRY(cudaMemcpyAsync(u, d_u, d * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LBM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return LBM_OK;
+}
+
 extern "C" int lbm_moments_batch(lbm_ctx* c, lbm_stats* stats, int flags, void* stream) {
     if (!c || !stats) return fail(LBM_ERR_ARG, "NULL argument");
     cudaStream_t s = S(stream);

@@ -27,7 +27,7 @@ LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
 EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
             "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc",
             "lbm_build_tilemap_batch", "lbm_init_batch", "lbm_moments_batch", "lbm_export_pdfs_sample",
-            "lbm_num_samples")
+            "lbm_num_samples", "lbm_moments_sample")
 LBM_NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -89,6 +89,7 @@ def library(build: bool = True):
             lib.lbm_moments_batch.argtypes = [P, P, I, P]
             lib.lbm_export_pdfs_sample.argtypes = [P, I, P, I, P]
             lib.lbm_num_samples.argtypes = [P]
+            lib.lbm_moments_sample.argtypes = [P, I, P, P, I, P]
             lib.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
                 getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -221,6 +222,10 @@ def lbm_moments_batch(ctx, n_samples, flags=0, stream=None):
     if rc not in (LBM_OK, -5):
         _check(rc)
     return list(arr), rc
+
+
+def lbm_moments_sample(ctx, sample, rho=None, u=None, flags=0, stream=None):
+    return _check(library().lbm_moments_sample(ctx, int(sample), _ptr(rho), _ptr(u), int(flags), stream))
 
 
 def lbm_export_pdfs_sample(ctx, sample, out, flags=0, stream=None):

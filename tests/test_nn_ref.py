@@ -1,0 +1,61 @@
+"""Pins of the FP64 reference of the warm-start network's operations."""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from oracle import nn_ref as R
+
+
+def test_conv_matches_scipy_correlate():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(1, 5, 6, 7, 1))
+    w = rng.normal(size=(27, 1, 1))
+    k = w[:, 0, 0].reshape(3, 3, 3)  # k[dz, dy, dx]
+    ref = ndimage.correlate(x[0, :, :, :, 0], k, mode="constant", cval=0.0)
+    assert np.allclose(R.conv3d(x, w)[0, :, :, :, 0], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_conv_adjoint_identities():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 4, 5, 6, 3))
+    w = rng.normal(size=(27, 3, 4))
+    dy = rng.normal(size=(2, 4, 5, 6, 4))
+    # <conv(x), dy> = <x, conv^T(dy)> = <w, dW(x, dy)>
+    lhs = np.sum(R.conv3d(x, w) * dy)
+    assert np.sum(x * R.conv3d_bwd_data(dy, w)) == pytest.approx(lhs, rel=1e-12)
+    dw, db = R.conv3d_bwd_weight(x, dy)
+    assert np.sum(w * dw) == pytest.approx(lhs, rel=1e-12)
+    assert np.allclose(db, dy.sum(axis=(0, 1, 2, 3)))
+
+
+def test_conv_gradients_by_finite_differences():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(1, 3, 4, 3, 2))
+    w = rng.normal(size=(27, 2, 2))
+    b = rng.normal(size=2)
+    dy = rng.normal(size=(1, 3, 4, 3, 2))
+    L = lambda w_, b_: np.sum(R.conv3d(x, w_, b_) * dy)
+    dw, db = R.conv3d_bwd_weight(x, dy)
+    for (t, i, o) in [(0, 0, 0), (13, 1, 0), (26, 0, 1), (5, 1, 1)]:
+        e = np.zeros_like(w)
+        e[t, i, o] = 1e-6
+        assert (L(w + e, b) - L(w - e, b)) / 2e-6 == pytest.approx(dw[t, i, o], rel=1e-6, abs=1e-9)
+    e = np.array([0.0, 1e-6])
+    assert (L(w, b + e) - L(w, b - e)) / 2e-6 == pytest.approx(db[1], rel=1e-6)
+
+
+def test_pool_and_upsample_adjoints():
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(2, 4, 6, 8, 3))
+    y = rng.normal(size=(2, 2, 3, 4, 3))
+    assert np.sum(R.pool2(x) * y) == pytest.approx(np.sum(x * R.pool2_bwd(y)), rel=1e-12)
+    assert np.sum(R.up2(y) * x) == pytest.approx(np.sum(y * R.up2_bwd(x)), rel=1e-12)
+    assert np.allclose(R.pool2(R.up2(y)), y)
+
+
+def test_bf16_rounding():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 2 ** -7 + 2 ** -9, -3.14159, 0.0])
+    r = R.bf16_round(v)
+    assert r[0] == 1.0 and r[1] == 1.0  # tie to even
+    assert r[2] == 1.0 + 2 ** -7
+    assert abs(r[3] + 3.14159) < 2 ** -7 * 4
