@@ -29,19 +29,24 @@ extern "C" {
 #endif
 
 /* y[p][co] = act( sum_{tap,ci} wgt[tap][ci][co] * x[p + off(tap)][ci] + bias[co] ),
- * act = ReLU when relu != 0.  Output BF16 (y) and/or FP32 (y32); either may
- * be NULL.  cout <= 128.  The backward-data pass is this same call on dy with
- * the weights from lbm_nn_weight_flip. */
+ * act = ReLU when relu != 0; bias may be NULL.  x[p + off] is zero outside the
+ * box except along the axes set in `wrap` (bit 0 = x, bit 1 = y, bit 2 = z),
+ * which are periodic.  Output BF16 (y) and/or FP32 (y32); either may be NULL.
+ * Any cout (output channels are tiled over the grid).  The backward-data pass
+ * is this same call on dy with the weights from lbm_nn_weight_flip and the
+ * same `wrap`. */
 int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
-                  const float* bias, int cout, int relu, void* y, float* y32, void* stream);
+                  const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
 
 /* dx-ready weights: wt[tap][co][ci] = wgt[26 - tap][ci][co] (BF16). */
 int lbm_nn_weight_flip(const void* wgt, int cin, int cout, void* wt, void* stream);
 
-/* dw[tap][ci][co] += sum_p x[p + off(tap)][ci] * dy[p][co] and, when dbias
- * is not NULL, dbias[co] += sum_p dy[p][co] (FP32 accumulators). */
+/* dw[tap][ci][co] += sum_p x[p + off(tap)][ci] * dy[p][co] (off and `wrap`
+ * as in lbm_nn_conv3d) and, when dbias is not NULL, dbias[co] += sum_p
+ * dy[p][co] (FP32 accumulators; the sums over voxel chunks are added
+ * atomically, so the last bits depend on their order). */
 int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout,
-                        float* dw, float* dbias, void* stream);
+                        int wrap, float* dw, float* dbias, void* stream);
 
 /* g[i] *= (act[i] > 0), over count BF16 values (ReLU backward in place). */
 int lbm_nn_relu_mask(void* g, const void* act, size_t count, void* stream);
@@ -69,6 +74,24 @@ int lbm_nn_mse(const float* pred, const float* target, const uint8_t* mask, size
  * buffers m, v, writing the BF16 copy pb.  t is the step number (1-based). */
 int lbm_nn_adam(float* p, float* g, float* m, float* v, void* pb, size_t count, float lr, float beta1,
                 float beta2, float eps, int t, void* stream);
+
+/* y = a + b over count BF16 values (y may alias a or b). */
+int lbm_nn_add(const void* a, const void* b, size_t count, void* y, void* stream);
+
+/* Network input from a geometry: x[v] = (mask[v] != 0, value) as two BF16
+ * channels (value = the body-force channel, F / 1e-6). */
+int lbm_nn_mask_input(const uint8_t* mask, size_t voxels, float value, void* x, void* stream);
+
+/* Training target from steady moments (dense FP64 rho[v] and u[c][v] as
+ * lbm_moments writes them): t[v] = ((rho - rho0) / s_rho, u_x / s_u, u_y / s_u,
+ * u_z / s_u) in FP32; 0 where rho or u is not finite (solid nodes). */
+int lbm_nn_fields_to_target(const double* rho, const double* u, size_t voxels, double rho0,
+                            double s_rho, double s_u, float* t, void* stream);
+
+/* The inverse: warm-start fields rho[v] = rho0 + s_rho t[v][0] and
+ * u[c][v] = s_u t[v][1 + c] (FP64, the layout lbm_init reads). */
+int lbm_nn_target_to_fields(const float* t, size_t voxels, double rho0, double s_rho, double s_u,
+                            double* rho, double* u, void* stream);
 
 /* Format conversions. */
 int lbm_nn_f32_to_bf16(const float* x, size_t count, void* y, void* stream);

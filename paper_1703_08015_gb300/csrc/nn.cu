@@ -28,18 +28,31 @@ constexpr int BM = 64;  // GEMM rows per block
 constexpr int BK = 32;  // reduction depth per shared-memory stage
 constexpr int LD = BK + 8;
 
-// C[p][co] = sum_k A[p][k] B[k][co], A[p][(tap,ci)] = x[p + off(tap)][ci] (0 outside),
-// B[(tap,ci)][co] = wgt[tap][ci][co]; one block computes 64 voxels x NF*8 outputs.
-template <int NF>
+// Neighbour coordinate along one axis with zero padding (returns -1 outside)
+// or periodic wrap.
+__device__ __forceinline__ int nb_coord(int c, int d, int n, bool wrap) {
+    c += d;
+    if (wrap) return c < 0 ? c + n : (c >= n ? c - n : c);
+    return (c < 0 || c >= n) ? -1 : c;
+}
+
+// C[p][co] = sum_k A[p][k] B[k][co], A[p][(tap,ci)] = x[p + off(tap)][ci] (0 outside,
+// or wrapped on the axes set in `wrap`), B[(tap,ci)][co] = wgt[tap][ci][co]; one
+// block computes 64 voxels x NF*8 outputs starting at channel blockIdx.y * NF*8.
+// VEC: Cin % 16 == 0, so that a thread's 16 consecutive k share one tap and are
+// read as two 16-byte vectors.
+template <int NF, bool VEC>
 __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N, int D, int H, int W, int Cin,
                                               const bf16* __restrict__ wgt, const float* __restrict__ bias,
-                                              int Cout, int relu, bf16* __restrict__ y, float* __restrict__ y32) {
+                                              int Cout, int relu, int wrap, bf16* __restrict__ y,
+                                              float* __restrict__ y32) {
     constexpr int BN = NF * 8;
     __shared__ __align__(16) bf16 As[BM][LD];
     __shared__ __align__(16) bf16 Bs[BN][LD];
     const long long M = (long long)N * D * H * W;
     const int K = 27 * Cin;
     const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float acc[NF][4];
 #pragma unroll
@@ -59,29 +72,47 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N,
         az = (int)(t % D);
         an = (int)(t / D);
     }
+    const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
     const bf16 zero = __float2bfloat16(0.f);
     for (int k0 = 0; k0 < K; k0 += BK) {
         int k = k0 + ak;
-        int tap = k / Cin, ci = k - tap * Cin;
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            bf16 v = zero;
+        if (VEC) {
+            uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
             if (arow && k < K) {
-                const int zz = az + tap / 9 - 1, yy = ay + (tap / 3) % 3 - 1, xx = ax + tap % 3 - 1;
-                if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    v = x[((((long long)an * D + zz) * H + yy) * W + xx) * Cin + ci];
+                const int tap = k / Cin, ci = k - tap * Cin;
+                const int zz = nb_coord(az, tap / 9 - 1, D, wz), yy = nb_coord(ay, (tap / 3) % 3 - 1, H, wy),
+                          xx = nb_coord(ax, tap % 3 - 1, W, wx);
+                if ((zz | yy | xx) >= 0) {
+                    const uint4* src =
+                        reinterpret_cast<const uint4*>(x + ((((long long)an * D + zz) * H + yy) * W + xx) * Cin + ci);
+                    v0 = src[0];
+                    v1 = src[1];
+                }
             }
-            As[ar][ak + j] = v;
-            k++;
-            if (++ci == Cin) {
-                ci = 0;
-                tap++;
+            *reinterpret_cast<uint4*>(&As[ar][ak]) = v0;
+            *reinterpret_cast<uint4*>(&As[ar][ak + 8]) = v1;
+        } else {
+            int tap = k / Cin, ci = k - tap * Cin;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                bf16 v = zero;
+                if (arow && k < K) {
+                    const int zz = nb_coord(az, tap / 9 - 1, D, wz), yy = nb_coord(ay, (tap / 3) % 3 - 1, H, wy),
+                              xx = nb_coord(ax, tap % 3 - 1, W, wx);
+                    if ((zz | yy | xx) >= 0) v = x[((((long long)an * D + zz) * H + yy) * W + xx) * Cin + ci];
+                }
+                As[ar][ak + j] = v;
+                k++;
+                if (++ci == Cin) {
+                    ci = 0;
+                    tap++;
+                }
             }
         }
         for (int e = tid; e < BN * BK; e += 128) {
             const int kk = e / BN, nn = e - kk * BN;
             const int kg = k0 + kk;
-            Bs[nn][kk] = (kg < K && nn < Cout) ? wgt[(long long)kg * Cout + nn] : zero;
+            Bs[nn][kk] = (kg < K && n0 + nn < Cout) ? wgt[(long long)kg * Cout + n0 + nn] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -105,7 +136,7 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N,
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 const long long row = m0 + warp * 16 + (lane >> 2) + h2 * 8;
-                const int co = f * 8 + (lane & 3) * 2 + j;
+                const int co = n0 + f * 8 + (lane & 3) * 2 + j;
                 if (row < M && co < Cout) {
                     float v = acc[f][h2 * 2 + j] + (bias ? bias[co] : 0.f);
                     if (relu) v = fmaxf(v, 0.f);
@@ -116,11 +147,12 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N,
 }
 
 // dW[(tap,ci)][co] += sum_p x[p + off(tap)][ci] dy[p][co]: GEMM with 64 rows of
-// (tap, ci) per block, NF*8 output channels, split over voxel chunks.
+// (tap, ci) per block, NF*8 output channels from blockIdx.z * NF*8, split over
+// voxel chunks (blockIdx.y) whose partial sums are added atomically.
 template <int NF>
 __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int N,
-                                               int D, int H, int W, int Cin, int Cout, float* __restrict__ dw,
-                                               long long vox_per_block) {
+                                               int D, int H, int W, int Cin, int Cout, int wrap,
+                                               float* __restrict__ dw, long long vox_per_block) {
     constexpr int BN = NF * 8;
     __shared__ __align__(16) bf16 As[BM][LD];  // [k row][voxel]
     __shared__ __align__(16) bf16 Bs[BN][LD];  // [co][voxel]
@@ -128,6 +160,7 @@ __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const
     const long long M = (long long)N * D * H * W;
     const int K = 27 * Cin;
     const int k0 = blockIdx.x * BM;
+    const int n0 = blockIdx.z * BN;
     const long long v_begin = (long long)blockIdx.y * vox_per_block;
     const long long v_end = v_begin + vox_per_block < M ? v_begin + vox_per_block : M;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -140,6 +173,7 @@ __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const
     const bool krow = kg < K;
     const int tap = krow ? kg / Cin : 0, ci = krow ? kg - tap * Cin : 0;
     const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
     const bf16 zero = __float2bfloat16(0.f);
     for (long long v0 = v_begin; v0 < v_end; v0 += BK) {
         if (tid < BK) {
@@ -163,16 +197,16 @@ __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const
             bf16 val = zero;
             const int n = vpos[vv][0];
             if (krow && n >= 0) {
-                const int zz = vpos[vv][1] + dz, yy = vpos[vv][2] + dyy, xx = vpos[vv][3] + dx;
-                if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    val = x[((((long long)n * D + zz) * H + yy) * W + xx) * Cin + ci];
+                const int zz = nb_coord(vpos[vv][1], dz, D, wz), yy = nb_coord(vpos[vv][2], dyy, H, wy),
+                          xx = nb_coord(vpos[vv][3], dx, W, wx);
+                if ((zz | yy | xx) >= 0) val = x[((((long long)n * D + zz) * H + yy) * W + xx) * Cin + ci];
             }
             As[kr][vv] = val;
         }
         for (int e = tid; e < BN * BK; e += 128) {
             const int vv = e / BN, nn = e - vv * BN;
             const long long v = v0 + vv;
-            Bs[nn][vv] = (v < v_end && nn < Cout) ? dy[v * Cout + nn] : zero;
+            Bs[nn][vv] = (v < v_end && n0 + nn < Cout) ? dy[v * Cout + n0 + nn] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -196,7 +230,7 @@ __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 const int row = k0 + warp * 16 + (lane >> 2) + h2 * 8;
-                const int co = f * 8 + (lane & 3) * 2 + j;
+                const int co = n0 + f * 8 + (lane & 3) * 2 + j;
                 if (row < K && co < Cout) atomicAdd(&dw[(long long)row * Cout + co], acc[f][h2 * 2 + j]);
             }
 }
@@ -355,6 +389,39 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __re
     }
 }
 
+__global__ void k_add(const bf16* __restrict__ a, const bf16* __restrict__ b, size_t n, bf16* __restrict__ y) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = __float2bfloat16(__bfloat162float(a[e]) + __bfloat162float(b[e]));
+}
+
+__global__ void k_mask_input(const uint8_t* __restrict__ mask, size_t vox, float value, bf16* __restrict__ x) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < vox; v += (size_t)gridDim.x * blockDim.x) {
+        x[2 * v] = __float2bfloat16(mask[v] ? 1.f : 0.f);
+        x[2 * v + 1] = __float2bfloat16(value);
+    }
+}
+
+__global__ void k_fields_to_target(const double* __restrict__ rho, const double* __restrict__ u, size_t vox,
+                                   double rho0, double inv_s_rho, double inv_s_u, float* __restrict__ t) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < vox; v += (size_t)gridDim.x * blockDim.x) {
+        double r = rho[v];
+        const bool ok = isfinite(r);
+        t[4 * v] = ok ? (float)((r - rho0) * inv_s_rho) : 0.f;
+        for (int c = 0; c < 3; c++) {
+            const double uc = u[c * vox + v];
+            t[4 * v + 1 + c] = ok && isfinite(uc) ? (float)(uc * inv_s_u) : 0.f;
+        }
+    }
+}
+
+__global__ void k_target_to_fields(const float* __restrict__ t, size_t vox, double rho0, double s_rho, double s_u,
+                                   double* __restrict__ rho, double* __restrict__ u) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < vox; v += (size_t)gridDim.x * blockDim.x) {
+        rho[v] = rho0 + s_rho * (double)t[4 * v];
+        for (int c = 0; c < 3; c++) u[c * vox + v] = s_u * (double)t[4 * v + 1 + c];
+    }
+}
+
 __global__ void k_f2b(const float* __restrict__ x, size_t n, bf16* __restrict__ y) {
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         y[e] = __float2bfloat16(x[e]);
@@ -380,24 +447,51 @@ static int check(cudaError_t e, const char* what) { return e == cudaSuccess ? LB
 using namespace lbm;
 using namespace lbm::nn;
 
+// Output-channel tiling shared by the forward and weight-gradient GEMMs: the
+// channels are split into equal tiles of at most 128, each a multiple of 8.
+static int pick_nf(int cout, int* n_tiles) {
+    const int tiles = (cout + 127) / 128;
+    const int per = (cout + tiles - 1) / tiles;
+    const int need = (per + 7) / 8;
+    static const int sizes[] = {1, 2, 4, 6, 8, 12, 16};
+    int nf = 16;
+    for (int s : sizes)
+        if (s >= need) {
+            nf = s;
+            break;
+        }
+    *n_tiles = (cout + nf * 8 - 1) / (nf * 8);
+    return nf;
+}
+
 extern "C" int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
-                             const float* bias, int cout, int relu, void* y, float* y32, void* stream) {
-    if (!x || !wgt || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || cout > 128 || (!y && !y32))
+                             const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream) {
+    if (!x || !wgt || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (!y && !y32) || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d: bad arguments");
     const long long M = (long long)n * d * h * w;
-    const unsigned grid = (unsigned)((M + BM - 1) / BM);
-    auto args = [&](auto kern) {
+    int ny = 0;
+    const int nf = pick_nf(cout, &ny);
+    const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)ny);
+    const bool vec = cin % 16 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    auto go = [&](auto kern) {
         kern<<<grid, 128, 0, S(stream)>>>(static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt),
-                                          bias, cout, relu, static_cast<bf16*>(y), y32);
+                                          bias, cout, relu, wrap, static_cast<bf16*>(y), y32);
     };
-    const int nf = (cout + 7) / 8;
-    if (nf <= 1) args(k_conv<1>);
-    else if (nf <= 2) args(k_conv<2>);
-    else if (nf <= 4) args(k_conv<4>);
-    else if (nf <= 6) args(k_conv<6>);
-    else if (nf <= 8) args(k_conv<8>);
-    else if (nf <= 12) args(k_conv<12>);
-    else args(k_conv<16>);
+#define LBM_NN_CONV(NF_)                         \
+    case NF_:                                   \
+        if (vec) go(k_conv<NF_, true>);         \
+        else go(k_conv<NF_, false>);            \
+        break;
+    switch (nf) {
+        LBM_NN_CONV(1)
+        LBM_NN_CONV(2)
+        LBM_NN_CONV(4)
+        LBM_NN_CONV(6)
+        LBM_NN_CONV(8)
+        LBM_NN_CONV(12)
+        LBM_NN_CONV(16)
+    }
+#undef LBM_NN_CONV
     return check(cudaGetLastError(), "k_conv launch");
 }
 
@@ -409,25 +503,28 @@ extern "C" int lbm_nn_weight_flip(const void* wgt, int cin, int cout, void* wt, 
 }
 
 extern "C" int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout,
-                                   float* dw, float* dbias, void* stream) {
-    if (!x || !dy || !dw || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || cout > 128)
+                                   int wrap, float* dw, float* dbias, void* stream) {
+    if (!x || !dy || !dw || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_wgrad: bad arguments");
     const long long M = (long long)n * d * h * w;
     const int K = 27 * cin;
     const long long vpb = 8192;
-    const dim3 grid((unsigned)((K + BM - 1) / BM), (unsigned)((M + vpb - 1) / vpb));
-    auto args = [&](auto kern) {
+    int nz = 0;
+    const int nf = pick_nf(cout, &nz);
+    const dim3 grid((unsigned)((K + BM - 1) / BM), (unsigned)((M + vpb - 1) / vpb), (unsigned)nz);
+    auto go = [&](auto kern) {
         kern<<<grid, 128, 0, S(stream)>>>(static_cast<const bf16*>(x), static_cast<const bf16*>(dy), n, d, h, w, cin,
-                                          cout, dw, vpb);
+                                          cout, wrap, dw, vpb);
     };
-    const int nf = (cout + 7) / 8;
-    if (nf <= 1) args(k_wgrad<1>);
-    else if (nf <= 2) args(k_wgrad<2>);
-    else if (nf <= 4) args(k_wgrad<4>);
-    else if (nf <= 6) args(k_wgrad<6>);
-    else if (nf <= 8) args(k_wgrad<8>);
-    else if (nf <= 12) args(k_wgrad<12>);
-    else args(k_wgrad<16>);
+    switch (nf) {
+        case 1: go(k_wgrad<1>); break;
+        case 2: go(k_wgrad<2>); break;
+        case 4: go(k_wgrad<4>); break;
+        case 6: go(k_wgrad<6>); break;
+        case 8: go(k_wgrad<8>); break;
+        case 12: go(k_wgrad<12>); break;
+        default: go(k_wgrad<16>); break;
+    }
     int rc = check(cudaGetLastError(), "k_wgrad launch");
     if (rc || !dbias) return rc;
     const long long rpb = 4096;
@@ -502,6 +599,34 @@ extern "C" int lbm_nn_adam(float* p, float* g, float* m, float* v, void* pb, siz
     k_adam<<<grid_for(count), 256, 0, S(stream)>>>(p, g, m, v, static_cast<bf16*>(pb), count, lr, beta1, beta2, eps,
                                                    c1, c2);
     return check(cudaGetLastError(), "k_adam launch");
+}
+
+extern "C" int lbm_nn_add(const void* a, const void* b, size_t count, void* y, void* stream) {
+    if (!a || !b || !y) return fail(LBM_ERR_ARG, "lbm_nn_add: NULL");
+    k_add<<<grid_for(count), 256, 0, S(stream)>>>(static_cast<const bf16*>(a), static_cast<const bf16*>(b), count,
+                                                  static_cast<bf16*>(y));
+    return check(cudaGetLastError(), "k_add launch");
+}
+
+extern "C" int lbm_nn_mask_input(const uint8_t* mask, size_t voxels, float value, void* x, void* stream) {
+    if (!mask || !x) return fail(LBM_ERR_ARG, "lbm_nn_mask_input: NULL");
+    k_mask_input<<<grid_for(voxels), 256, 0, S(stream)>>>(mask, voxels, value, static_cast<bf16*>(x));
+    return check(cudaGetLastError(), "k_mask_input launch");
+}
+
+extern "C" int lbm_nn_fields_to_target(const double* rho, const double* u, size_t voxels, double rho0,
+                                       double s_rho, double s_u, float* t, void* stream) {
+    if (!rho || !u || !t || !(s_rho != 0.0) || !(s_u != 0.0))
+        return fail(LBM_ERR_ARG, "lbm_nn_fields_to_target: bad arguments");
+    k_fields_to_target<<<grid_for(voxels), 256, 0, S(stream)>>>(rho, u, voxels, rho0, 1.0 / s_rho, 1.0 / s_u, t);
+    return check(cudaGetLastError(), "k_fields_to_target launch");
+}
+
+extern "C" int lbm_nn_target_to_fields(const float* t, size_t voxels, double rho0, double s_rho, double s_u,
+                                       double* rho, double* u, void* stream) {
+    if (!t || !rho || !u) return fail(LBM_ERR_ARG, "lbm_nn_target_to_fields: NULL");
+    k_target_to_fields<<<grid_for(voxels), 256, 0, S(stream)>>>(t, voxels, rho0, s_rho, s_u, rho, u);
+    return check(cudaGetLastError(), "k_target_to_fields launch");
 }
 
 extern "C" int lbm_nn_f32_to_bf16(const float* x, size_t count, void* y, void* stream) {

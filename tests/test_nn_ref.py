@@ -59,3 +59,73 @@ def test_bf16_rounding():
     assert r[0] == 1.0 and r[1] == 1.0  # tie to even
     assert r[2] == 1.0 + 2 ** -7
     assert abs(r[3] + 3.14159) < 2 ** -7 * 4
+
+
+def test_periodic_conv_matches_scipy():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(1, 4, 5, 6, 1))
+    w = rng.normal(size=(27, 1, 1))
+    k = w[:, 0, 0].reshape(3, 3, 3)
+    # all axes periodic: scipy's wrap mode
+    ref = ndimage.correlate(x[0, :, :, :, 0], k, mode="wrap")
+    assert np.allclose(R.conv3d(x, w, wrap=7)[0, :, :, :, 0], ref, rtol=1e-12, atol=1e-12)
+    # x periodic only: three copies side by side along x, zero padding, middle copy
+    tiled = np.concatenate([x[0, :, :, :, 0]] * 3, axis=2)
+    ref = ndimage.correlate(tiled, k, mode="constant", cval=0.0)[:, :, 6:12]
+    assert np.allclose(R.conv3d(x, w, wrap=1)[0, :, :, :, 0], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_periodic_conv_adjoints():
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(2, 4, 3, 6, 3))
+    w = rng.normal(size=(27, 3, 2))
+    dy = rng.normal(size=(2, 4, 3, 6, 2))
+    for wrap in (1, 2, 5):
+        lhs = np.sum(R.conv3d(x, w, wrap=wrap) * dy)
+        assert np.sum(x * R.conv3d_bwd_data(dy, w, wrap=wrap)) == pytest.approx(lhs, rel=1e-12)
+        dw, _ = R.conv3d_bwd_weight(x, dy, wrap=wrap)
+        assert np.sum(w * dw) == pytest.approx(lhs, rel=1e-12)
+
+
+def _tiny_unet(rng, chans=(2, 3), cin=2, cout=2):
+    names = []
+    c = cin
+    for lv, ch in enumerate(chans[:-1]):
+        names += [(f"enc{lv}a", c, ch), (f"enc{lv}b", ch, ch)]
+        c = ch
+    names += [("mid_a", c, chans[-1]), ("mid_b", chans[-1], chans[-1])]
+    c = chans[-1]
+    for lv in reversed(range(len(chans) - 1)):
+        names += [(f"dec{lv}a", c + chans[lv], chans[lv]), (f"dec{lv}b", chans[lv], chans[lv])]
+        c = chans[lv]
+    names.append(("head", c, cout))
+    # positive biases keep most ReLUs active, so the finite differences see every path
+    return {n: (rng.normal(0, 0.5, (27, a, b)), rng.uniform(0.2, 0.6, b)) for n, a, b in names}
+
+
+def test_unet_gradients_by_finite_differences():
+    rng = np.random.default_rng(6)
+    chans = (2, 3)
+    params = _tiny_unet(rng, chans)
+    x = rng.normal(size=(1, 4, 4, 4, 2))
+    dy = rng.normal(size=(1, 4, 4, 4, 2))
+    y, cache = R.unet_forward(params, x, chans, wrap=1)
+    grads = R.unet_backward(params, cache, dy, chans, wrap=1)
+
+    def loss(p):
+        return np.sum(R.unet_forward(p, x, chans, wrap=1)[0] * dy)
+
+    h = 1e-6
+    for name in ("enc0a", "enc0b", "mid_a", "mid_b", "dec0a", "dec0b", "head"):
+        w, b = params[name]
+        for idx in [(0, 0, 0), (13, w.shape[1] - 1, w.shape[2] - 1), (22, 0, w.shape[2] - 1)]:
+            wp, wm = w.copy(), w.copy()
+            wp[idx] += h
+            wm[idx] -= h
+            fd = (loss({**params, name: (wp, b)}) - loss({**params, name: (wm, b)})) / (2 * h)
+            assert fd == pytest.approx(grads[name][0][idx], rel=1e-5, abs=1e-7), (name, idx)
+        bp, bm = b.copy(), b.copy()
+        bp[0] += h
+        bm[0] -= h
+        fd = (loss({**params, name: (w, bp)}) - loss({**params, name: (w, bm)})) / (2 * h)
+        assert fd == pytest.approx(grads[name][1][0], rel=1e-5, abs=1e-7), name
