@@ -78,16 +78,16 @@ struct FixedConsts {
 };
 
 // Constants of the float-float FP64 path: each a (hi, lo) pair of floats.
-struct FFConsts {
-    float2 w[3];       // w_c
-    float2 rho[3];     // w * w_c
-    float2 j[3];       // 3 w w_c
+struct FFConsts {      // u_c = 1 / ulp(w_c): class quantities in ulps of w_c
+    float2 w[3];       // w_c u_c
+    float2 rho[3];     // w * w_c u_c
+    float2 j[3];       // 3 w w_c u_c
     float2 keep;       // 1 - w
     float2 alpha;      // 4.5 w
     float2 g1;         // 1.5 w
     float2 kf[3];      // 3 (1 - w/2) F_a
     float2 beta[19];   // 9 (1 - w/2) (c_i.F)
-    float2 so[19];     // 3 (1 - w/2) w_i (c_i.F)
+    float2 so[19];     // 3 (1 - w/2) w_i (c_i.F) u_c
 };
 
 struct StepArgs {

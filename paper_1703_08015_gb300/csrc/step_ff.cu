@@ -11,8 +11,10 @@
 //     d_i convert to FP32 exactly when |d_i| < 2^47;
 //   * rho - 1 and j are exact 64-bit integer sums (units of 2^-60), converted
 //     to float-float once per node;
-//   * every f*_i is rounded once to FP64 (faithfully: within one unit of the
-//     last place of the exact float-float result).
+//   * every quantity of link class c is formed directly in units of
+//     ulp(w_c) (the scale is folded into the constants), and every f*_i is
+//     rounded once to FP64: the integer count of ulps is taken within one unit
+//     of the float-float result.
 // Nodes outside that range (|f_i - w_i| beyond ~w_i/32, |j| >= 1/16,
 // |rho - 1| >= 1/32, NaN, negative values) are recomputed in native FP64.
 #include <cmath>
@@ -99,8 +101,6 @@ struct FFLink {
     using K = Link<L, I>;
     static constexpr int E = fp_exp(K::w);  // binade of w_i: ulp(w_i) = 2^(E - 52)
     static constexpr int SHIFT = E + 8;     // d << SHIFT is g in units of 2^-60
-    static constexpr float HI = pow2f(E - 28), LO = pow2f(E - 52), TO_ULP = pow2f(52 - E);
-    static constexpr int REP = I < K::opp ? I : K::opp;
 };
 
 __device__ __forceinline__ bool small_ll(long long x, int log2bound) {
@@ -116,20 +116,24 @@ __device__ __forceinline__ ff q60_to_ff(long long x) {
     return fast2(s.h, __fadd_rn(s.l, f0));
 }
 
-// FP64 bit pattern of w + x * 2^(E-52), x given as float-float in units of
-// ulp(w) (|x| < 2^48); the integer is taken within one unit of the exact x.
-__device__ __forceinline__ unsigned long long ulp_to_bits(ff x, unsigned long long wb, bool& ok) {
-    const float rh = rintf(x.h);
-    const float t = __fadd_rn(__fsub_rn(x.h, rh), x.l);
-    const int k = __float_as_int(__fadd_rn(t, 12582912.f)) - 0x4B400000;  // rint(t), |t| < 2^22
-    const unsigned bits = __float_as_uint(rh);
-    const int e = (int)((bits >> 23) & 0xFF);
-    const unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u) << 24;
-    ok &= e <= 174;  // |rh| < 2^48
-    const unsigned long long mag = (e >= 127 && e <= 174) ? m >> (174 - e) : 0ull;
-    const long long v = (bits >> 31) ? -(long long)mag : (long long)mag;
-    const unsigned long long out = wb + (unsigned long long)(v + k);
-    ok &= ((out ^ wb) >> 52) == 0;
+// a + b + c with the rounding errors of both high-part sums kept in the low
+// part (not renormalised: ulp_round takes any low part below 2^30).
+__device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
+    const ff s = two_sum(a.h, b.h);
+    const ff t = two_sum(s.h, c.h);
+    return ff{t.h, __fadd_rn(__fadd_rn(__fadd_rn(a.l, b.l), __fadd_rn(c.l, s.l)), t.l)};
+}
+
+// FP64 bit pattern of w + r ulp(w) with r the integer within one unit of
+// x = x.h + x.l (units of ulp(w)): x.h splits exactly into hi 2^24 + rem, and
+// rem and x.l are rounded to integers separately.
+__device__ __forceinline__ unsigned long long ulp_round(ff x, unsigned long long wb, bool& ok) {
+    ok &= fabsf(x.h) < pow2f(47) && fabsf(x.l) < pow2f(30);
+    const int hi = __float2int_rz(__fmul_rn(x.h, pow2f(-24)));            // |hi| < 2^23
+    const float rem = __fmaf_rn(__int2float_rn(hi), -pow2f(24), x.h);     // exact, |rem| < 2^24
+    const int lo = __float2int_rn(rem) + __float2int_rn(x.l);
+    const unsigned long long out = wb + (unsigned long long)(((long long)hi << 24) + (long long)lo);
+    ok &= ((out ^ wb) >> 52) == 0;  // same sign and binade as w
     return out;
 }
 
@@ -151,19 +155,26 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         d[i] = (long long)(b[i] - (unsigned long long)k.w_bits[Link<L, i>::cls]);
         ok &= small_ll(d[i], 47);  // also rejects another binade, sign, NaN/Inf
     });
-    long long dr = k.dws, jx = k.half_f[0], jy = k.half_f[1], jz = k.half_f[2];
+    // exact sums per class (units of ulp(w_c)), then one shift per class to 2^-60
+    long long sr[3] = {0, 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         using K = Link<L, i>;
-        const long long g = d[i] << FFLink<L, i>::SHIFT;
-        dr += g;
-        if constexpr (K::cx > 0) jx += g;
-        if constexpr (K::cx < 0) jx -= g;
-        if constexpr (K::cy > 0) jy += g;
-        if constexpr (K::cy < 0) jy -= g;
-        if constexpr (K::cz > 0) jz += g;
-        if constexpr (K::cz < 0) jz -= g;
+        constexpr int cl = K::cls;
+        sr[cl] += d[i];
+        if constexpr (K::cx > 0) sx[cl] += d[i];
+        if constexpr (K::cx < 0) sx[cl] -= d[i];
+        if constexpr (K::cy > 0) sy[cl] += d[i];
+        if constexpr (K::cy < 0) sy[cl] -= d[i];
+        if constexpr (K::cz > 0) sz[cl] += d[i];
+        if constexpr (K::cz < 0) sz[cl] -= d[i];
     });
+    constexpr int S0 = FFLink<L, ff_first_of_class<L, 0>()>::SHIFT, S1 = FFLink<L, ff_first_of_class<L, 1>()>::SHIFT,
+                  S2 = FFLink<L, ff_first_of_class<L, 2>()>::SHIFT;
+    const long long dr = k.dws + (sr[0] << S0) + (sr[1] << S1) + (sr[2] << S2);
+    const long long jx = k.half_f[0] + (sx[1] << S1) + (sx[2] << S2);
+    const long long jy = k.half_f[1] + (sy[1] << S1) + (sy[2] << S2);
+    const long long jz = k.half_f[2] + (sz[1] << S1) + (sz[2] << S2);
     ok &= small_ll(dr, 55) & small_ll(jx, 56) & small_ll(jy, 56) & small_ll(jz, 56);
     if (!ok) return false;
 
@@ -180,58 +191,56 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         const float er = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(rho.l, r0));
         RINV = fast2(r0, __fmul_rn(r0, er));
     }
+    // gamma = 1.5 w |p|^2 + 3 (1 - w/2) p.F, p = j + F/2
     const ff jj = ff_add(ff_add(ff_sqr(JX), ff_sqr(JY)), ff_sqr(JZ));
     const ff gamma = ff_add(ff_mul(jj, ff_c(c.g1)),
                             ff_add(ff_add(ff_mul(JX, ff_c(c.kf[0])), ff_mul(JY, ff_c(c.kf[1]))),
                                    ff_mul(JZ, ff_c(c.kf[2]))));
-    auto emit = [&](auto I, ff s) {
-        constexpr int i = decltype(I)::value;
-        constexpr float sc = FFLink<L, i>::TO_ULP;
-        const ff x{__fmul_rn(s.h, sc), __fmul_rn(s.l, sc)};
-        out[i * stride] = ulp_to_bits(x, (unsigned long long)k.w_bits[Link<L, i>::cls], ok);
-    };
-    auto link_ff = [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        using F = FFLink<L, i>;
-        return ff{__fmul_rn(__int2float_rn((int)(d[i] >> 24)), F::HI),
-                  __fmul_rn(__int2float_rn((int)(d[i] & 0xFFFFFF)), F::LO)};
-    };
+    // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V
+    ff V[3], C[3];
+    static_for<0, 3>([&](auto CL) {
+        constexpr int cl = decltype(CL)::value;
+        V[cl] = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[cl])) : ff_c(c.w[cl]);
+        C[cl] = ff_add(ff_mul(DR, ff_c(c.rho[cl])), ff_neg(ff_mul(gamma, V[cl])));
+    });
     const ff KEEP = ff_c(c.keep);
-    ff R{0.f, 0.f}, V{0.f, 0.f}, PX{0.f, 0.f}, PY{0.f, 0.f}, PZ{0.f, 0.f};
+    // (1 - w) g_i in ulps: g_i = d_i ulp(w_i), d_i split into exact 24-bit halves
+    auto kept = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const ff g{__fmul_rn(__int2float_rn((int)(d[i] >> 24)), pow2f(24)), __int2float_rn((int)(d[i] & 0xFFFFFF))};
+        return ff_mul(g, KEEP);
+    };
+    auto store = [&](auto I, ff x) {
+        constexpr int i = decltype(I)::value;
+        out[i * stride] = ulp_round(x, (unsigned long long)k.w_bits[Link<L, i>::cls], ok);
+    };
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        using F = FFLink<L, i>;
         using K = Link<L, i>;
-        if constexpr (F::REP == i) {
+        if constexpr (i == 0) {
+            const ff x = ff_add(kept(I), C[0]);
+            store(I, x);
+        } else if constexpr (i < K::opp) {
+            constexpr int j = K::opp;
             constexpr int cl = K::cls;
-            if constexpr (i == ff_first_of_class<L, cl>()) {
-                R = ff_mul(DR, ff_c(c.rho[cl]));
-                V = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[cl])) : ff_c(c.w[cl]);
-                if constexpr (cl > 0) {
-                    PX = ff_mul(JX, ff_c(c.j[cl]));
-                    PY = ff_mul(JY, ff_c(c.j[cl]));
-                    if constexpr (L::D == 3) PZ = ff_mul(JZ, ff_c(c.j[cl]));
-                }
-            }
-            if constexpr (i == 0) {
-                emit(I, ff_add(ff_mul(link_ff(I), KEEP), ff_add(R, ff_mul(ff_neg(gamma), V))));
-            } else {
-                constexpr int j = K::opp;
-                ff Y{0.f, 0.f}, O = ff_c(c.so[i]);
-                auto acc = [&](int sgn, const ff& JA, const ff& PA) {
-                    Y = ff_add(Y, sgn > 0 ? JA : ff_neg(JA));
-                    O = ff_add(O, sgn > 0 ? PA : ff_neg(PA));
-                };
-                if constexpr (K::cx != 0) acc(K::cx, JX, PX);
-                if constexpr (K::cy != 0) acc(K::cy, JY, PY);
-                if constexpr (K::cz != 0) acc(K::cz, JZ, PZ);
-                const ff A = ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[i]));
-                const ff T = ff_mul(Y, A);
-                const ff E = ff_add(R, ff_mul(ff_add(T, ff_neg(gamma)), V));
-                emit(I, ff_add(ff_add(ff_mul(link_ff(I), KEEP), E), O));
-                emit(std::integral_constant<int, j>{},
-                     ff_add(ff_add(ff_mul(link_ff(std::integral_constant<int, j>{}), KEEP), E), ff_neg(O)));
-            }
+            // y = c_i . p
+            ff Y{0.f, 0.f};
+            bool first = true;
+            auto acc = [&](int sgn, const ff& JA) {
+                const ff t = sgn > 0 ? JA : ff_neg(JA);
+                Y = first ? t : ff_add(Y, t);
+                first = false;
+            };
+            if constexpr (K::cx != 0) acc(K::cx, JX);
+            if constexpr (K::cy != 0) acc(K::cy, JY);
+            if constexpr (K::cz != 0) acc(K::cz, JZ);
+            // symmetric part E = C + y (4.5 w y + 9 (1 - w/2) c_i.F) V, antisymmetric part
+            // O = 3 w w_c y + 3 (1 - w/2) w_c c_i.F (all in ulps of w_c)
+            const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[i])));
+            const ff E = ff_add(C[cl], ff_mul(T, V[cl]));
+            const ff O = ff_add(ff_mul(Y, ff_c(c.j[cl])), ff_c(c.so[i]));
+            store(I, ff_sum3(kept(I), E, O));
+            store(std::integral_constant<int, j>{}, ff_sum3(kept(std::integral_constant<int, j>{}), E, ff_neg(O)));
         }
     });
     return ok;
@@ -284,11 +293,18 @@ static void ff_consts_for(const lbm_params* p, FFConsts* k) {
     const double omega = 1.0 / p->tau;
     const double kf = 1.0 - 0.5 * omega;
     const double F[3] = {p->force[0], p->force[1], L::D == 3 ? p->force[2] : 0.0};
+    // class quantities in units of ulp(w_c) = 2^(E_c - 52) (exact power-of-two scales)
+    double to_ulp[3];
+    for (int c = 0; c < 3; c++) {
+        int e = 0;
+        std::frexp(L::wc_[c], &e);  // w_c = m 2^e, m in [1/2, 1): E_c = e - 1
+        to_ulp[c] = std::ldexp(1.0, 52 - (e - 1));
+    }
     for (int c = 0; c < 3; c++) {
         const double w = L::wc_[c];
-        k->w[c] = split(w);
-        k->rho[c] = split(omega * w);
-        k->j[c] = split(3.0 * omega * w);
+        k->w[c] = split(w * to_ulp[c]);
+        k->rho[c] = split(omega * w * to_ulp[c]);
+        k->j[c] = split(3.0 * omega * w * to_ulp[c]);
     }
     k->keep = split(1.0 - omega);
     k->alpha = split(4.5 * omega);
@@ -297,7 +313,7 @@ static void ff_consts_for(const lbm_params* p, FFConsts* k) {
     for (int i = 0; i < L::Q; i++) {
         const double cF = L::cx_[i] * F[0] + L::cy_[i] * F[1] + L::cz_[i] * F[2];
         k->beta[i] = split(9.0 * kf * cF);
-        k->so[i] = split(3.0 * kf * L::wc_[L::cls_[i]] * cF);
+        k->so[i] = split(3.0 * kf * L::wc_[L::cls_[i]] * cF * to_ulp[L::cls_[i]]);
     }
 }
 

@@ -58,6 +58,23 @@ __device__ __forceinline__ void stage_neighbourhood(NeighShared<TL, TPB>& sh, co
     }
 }
 
+// Fluid bit of node n and, when set, its rank (see fluid_rank): the word is
+// shifted so that bit n lands in the sign bit; the popcount then counts the
+// bits at and below n.
+template <int W>
+__device__ __forceinline__ int fluid_bit_rank(const uint64_t* m, int n, bool& fl) {
+    const unsigned long long t = (W == 1 ? m[0] : m[n >> 6]) << (63 - (n & 63));
+    fl = (long long)t < 0;
+    int r = __popcll(t) - (int)fl;
+    if constexpr (W > 1) {
+        const int w = n >> 6;
+#pragma unroll
+        for (int k = 0; k < W - 1; k++)
+            if (k < w) r += __popcll(m[k]);
+    }
+    return r;
+}
+
 template <class TL, int TPB>
 __device__ __forceinline__ bool mask_bit(const NeighShared<TL, TPB>& sh, int lt, int slot, int n) {
     if constexpr (TL::W == 1)
@@ -111,9 +128,9 @@ __device__ __forceinline__ int gather(const NeighShared<Tile<L, A>, TPB>& sh, in
     static_for<1, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const PullSource<L, A, i> s(p);
-        const bool fl = mask_bit(sh, lt, s.slot, s.sn);
-        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * sh.stride[lt][s.slot] +
-                                fluid_rank<TL::W>(sh.m[lt][s.slot], s.sn)
+        bool fl;
+        const int r = fluid_bit_rank<TL::W>(sh.m[lt][s.slot], s.sn, fl);
+        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * sh.stride[lt][s.slot] + r
                           : own + Link<L, i>::opp * own_stride + own_rank;
         f[i] = __ldg(src);
     });
