@@ -48,12 +48,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--arith", default="auto", choices=["auto", "f64", "fixed", "ff"])
     ap.add_argument("--storage", default="f64", choices=["f64", "f32", "f32s", "f16s"])
+    ap.add_argument("--layout", default="t2c", choices=["t2c", "tgb"],
+                    help="two PDF copies (T2C) or one copy with ghost buffers (TGB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="throughput", choices=["throughput", "steady", "batch"])
     ap.add_argument("--samples", type=int, default=64)
     ap.add_argument("--max-steps", type=int, default=100000)
     ap.add_argument("--target", type=float, default=1e-6)
+    ap.add_argument("--weights", default=None, help="warm-start network weights (steady mode)")
     return ap.parse_args()
 
 
@@ -112,10 +115,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+STEP_SOURCES = ("internal.h", "lattice.cuh", "tile.cuh", "collide_f64.cuh", "step_ff.cu", "step_fixed.cu",
+                "step_f64.cu", "step_f32.cu", "tiling.cpp")
+
+
 def kernel_source_sha():
+    """Hash of the sources the step kernels are built from (a committed traffic
+    figure is used only while they are unchanged)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1703_08015_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
+    for f in STEP_SOURCES:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -210,8 +219,9 @@ def run_ours(args):
              "ff": lbm.LBM_ARITH_FF}[args.arith]
     storage = {"f64": lbm.LBM_STORE_F64, "f32": lbm.LBM_STORE_F32, "f32s": lbm.LBM_STORE_F32S,
                "f16s": lbm.LBM_STORE_F16S}[args.storage]
+    layout = {"t2c": lbm.LBM_LAYOUT_T2C, "tgb": lbm.LBM_LAYOUT_TGB}[args.layout]
     solver = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], arith=arith,
-                        storage=storage, device=dev)
+                        storage=storage, layout=layout, device=dev)
     stream = solver.stream
     n_fluid = int(solver.tiling.n_fluid)
 
@@ -274,6 +284,7 @@ def run_ours(args):
     bytes_per_launch = n_fluid * pm.B_node(lat, s_d)
     achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
     traffic, tnote = committed_traffic(args.workload, arith_name)
+    dev_bytes = int(tiling.pdf_bytes) + (int(tiling.ghost_bytes) if args.layout == "tgb" else int(tiling.pdf_bytes))
     tiling_stats = {"n_ftiles": int(tiling.n_ftiles), "n_tiles": int(tiling.n_tiles),
                     "phi": n_fluid / mask.size,
                     "phi_t": n_fluid / (tiling.n_ftiles * a ** (3 if lat == 19 else 2))}
@@ -288,8 +299,12 @@ def run_ours(args):
                    "tau": params["tau"], "force": params["force"], "storage": args.storage,
                    "arith": arith_name if args.storage == "f64" else "f32",
                    "stats_every": STATS_EVERY, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (two PDF copies of "
-                         f"{tiling.pdf_bytes / 1e9:.2f} GB each, L2 129 MB)",
+                   "layout": args.layout,
+                   "pdf_device_bytes": dev_bytes,
+                   "l2": (f"inputs larger than L2 (PDF state {dev_bytes / 1e9:.2f} GB, L2 129 MB)"
+                          if dev_bytes > 129e6 else
+                          f"L2-resident small case (PDF state {dev_bytes / 1e6:.1f} MB < L2 129 MB): "
+                          "a latency figure, not an HBM measurement"),
                    "geometry": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -360,8 +375,11 @@ def ctypes_stream(stream):
 
 def run_steady(args):
     """Time to steady state (residual below --target, checked every 100 steps
-    with the FP64 reduction) for the FP64 path and the FP32 / FP16 storage
-    forms, from rest, on one GPU; errors of the reduced forms against FP64."""
+    with the FP64 reduction) on one GPU: the plain FP64 solve from rest (the
+    baseline), then every storage form with the period-2 filter
+    (lbm_filter_period2 after each residual check) and, when trained weights
+    are present, started from the warm-start network's prediction.  Errors of
+    every form against the filtered FP64 zero start."""
     import torch
 
     from paper_1703_08015_gb300 import lbm
@@ -373,17 +391,31 @@ def run_steady(args):
     lat, a = params["lattice"], params["tile_a"]
     nu = (params["tau"] - 0.5) / 3.0
     fx = params["force"][0]
-    forms = [("f64", lbm.LBM_STORE_F64), ("f32", lbm.LBM_STORE_F32), ("f32s", lbm.LBM_STORE_F32S),
-             ("f16s", lbm.LBM_STORE_F16S)]
-    res = {}
-    fields = {}
-    for name, storage in forms:
-        s = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], storage=storage,
-                       device=dev)
-        st0, _ = s.stats(residual=True)
+    net = None
+    weights = args.weights or os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1703_08015_gb300",
+                                           "weights", "unet_spheres64.npz")
+    if lat == 19 and os.path.exists(weights) and all(n % 8 == 0 for n in mask.shape):
+        from paper_1703_08015_gb300 import nn
+
+        net = nn.UNet.load(weights, device=dev)
+    S = lbm
+    forms = [("f64", S.LBM_STORE_F64, False, False), ("f64_p2", S.LBM_STORE_F64, True, False),
+             ("f32s", S.LBM_STORE_F32S, False, False), ("f32s_p2", S.LBM_STORE_F32S, True, False),
+             ("f32_p2", S.LBM_STORE_F32, True, False), ("f16s_p2", S.LBM_STORE_F16S, True, False)]
+    if net is not None:
+        forms += [("f64_warm_p2", S.LBM_STORE_F64, True, True), ("f32s_warm_p2", S.LBM_STORE_F32S, True, True)]
+    res, fields = {}, {}
+    fl = mask.astype(bool)
+    for name, storage, filt, warm in forms:
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        n, st, hist = 0, st0, []
+        rho0 = u0 = None
+        if warm:
+            rho0, u0 = nn.predict_fields(net, mask, fx, nu)
+        s = lbm.Solver(mask, lat, a, params["periodic"], params["tau"], params["force"], storage=storage,
+                       rho_init=rho0, u_init=u0, device=dev)
+        st0, _ = s.stats(residual=True)
+        n, st, hist, n_filter = 0, st0, [], 0
         while n < args.max_steps:
             s.step(STATS_EVERY)
             n += STATS_EVERY
@@ -391,33 +423,38 @@ def run_steady(args):
             hist.append(st.residual)
             if rc != 0 or st.residual < args.target:
                 break
+            if filt:
+                s.filter_period2()
+                n_filter += 1
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         rho, u, st_f, _ = s.moments()
         s.close()
-        fl = mask.astype(bool)
         k = nu * float(np.sum(u[0][fl])) / mask.size / fx if fx else None  # superficial-velocity permeability
         fields[name] = u[:, fl]
-        res[name] = {"steps": n, "seconds": dt, "converged": bool(st.residual < args.target),
+        res[name] = {"steps": n, "filters": n_filter, "seconds": dt, "converged": bool(st.residual < args.target),
                      "final_residual": st.residual, "mlups": int(st.n_fluid) * n / dt / 1e6,
                      "permeability": k, "mass_drift": abs(st.mass - st0.mass) / st0.mass,
                      "residual_floor": float(min(hist)) if hist else None}
-    ref = fields["f64"]
-    for name in ("f32", "f32s", "f16s"):
+    ref = fields["f64_p2"]
+    for name in res:
         d = fields[name] - ref
-        res[name]["velocity_l2_rel_err_vs_f64"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
-        if res["f64"]["permeability"]:
-            res[name]["permeability_rel_err_vs_f64"] = abs(res[name]["permeability"] / res["f64"]["permeability"] - 1)
+        res[name]["velocity_l2_rel_err_vs_f64_p2"] = float(np.sqrt(np.sum(d * d) / np.sum(ref * ref)))
+        if res["f64_p2"]["permeability"]:
+            res[name]["permeability_rel_err_vs_f64_p2"] = abs(res[name]["permeability"] /
+                                                              res["f64_p2"]["permeability"] - 1)
         res[name]["speedup_vs_f64"] = res["f64"]["seconds"] / res[name]["seconds"]
+    ok = [kk for kk, r in res.items() if kk != "f64" and r["converged"] and
+          r.get("permeability_rel_err_vs_f64_p2", 1.0) <= 1e-3]
+    best = min(ok, key=lambda kk: res[kk]["seconds"]) if ok else None
     if rank == 0:
         print(json.dumps({"metric": "time to steady state (residual < %g) vs plain FP64" % args.target,
-                          "value": res["f64"]["seconds"] / min(r["seconds"] for k, r in res.items()
-                                                               if k != "f64" and r["converged"])
-                          if any(r["converged"] for k, r in res.items() if k != "f64") else None,
-                          "unit": "x speedup of the fastest reduced form", "higher_is_better": True,
-                          "n_gpus": 1, "data": "synthetic",
+                          "value": res["f64"]["seconds"] / res[best]["seconds"] if best else None,
+                          "unit": "x speedup of the fastest form (permeability within 1e-3)",
+                          "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "best_form": best,
                           "config": {"workload": args.workload, "check_every": STATS_EVERY,
-                                     "max_steps": args.max_steps, "geometry": info},
+                                     "max_steps": args.max_steps, "geometry": info,
+                                     "warm_start_weights": os.path.basename(weights) if net is not None else None},
                           "forms": res}))
 
 

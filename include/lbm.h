@@ -80,6 +80,14 @@ extern "C" {
 #define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions */
 #define LBM_ARITH_FF     3 /* exact integer sums, float-float products (~48 bits), no FP64 instructions */
 
+/* PDF layouts (Sec. 3.1).  T2C: two copies, each step reads one and writes the
+ * other (Fig. 5).  TGB: one copy updated in place; values that cross a tile
+ * edge travel through two sets of ghost buffers (per tile and link, the nodes
+ * on the tile's downstream boundary), so the memory is one copy plus the
+ * ghost sets (lbm_tiling.ghost_bytes).  The update is the same bit for bit. */
+#define LBM_LAYOUT_T2C 0
+#define LBM_LAYOUT_TGB 1
+
 /* lbm_moments flags */
 #define LBM_OUT_DEVICE    1 /* rho/u/pdf pointers are device pointers (default: host) */
 #define LBM_STATS_RESIDUAL 2 /* compute the steady-state residual against the
@@ -105,6 +113,8 @@ typedef struct lbm_params {
                          FP32 storage forms with 4^3 / 8^2 tiles (autotuner choice) */
     int persistent;   /* 1 = FP32 storage forms run a persistent step kernel: as many
                          blocks as fit on the GPU at once loop over the work list */
+    int layout;       /* LBM_LAYOUT_T2C (two PDF copies, default) or LBM_LAYOUT_TGB
+                         (one copy updated in place plus ghost buffers, Sec. 3.1) */
 } lbm_params;
 
 typedef struct lbm_tiling {
@@ -114,6 +124,8 @@ typedef struct lbm_tiling {
     int32_t nbr_per_tile;  /* 3^d entries in each neighbour record */
     int64_t n_fluid;       /* N_fnodes, non-solid nodes (Eq. 11) */
     size_t pdf_bytes;      /* bytes of ONE PDF copy in the requested storage */
+    size_t ghost_bytes;    /* LBM_LAYOUT_TGB: bytes of the two ghost-buffer sets that
+                              pdf_b must hold (0 for LBM_LAYOUT_T2C) */
 } lbm_tiling;
 
 typedef struct lbm_stats {
@@ -154,6 +166,8 @@ int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask,
  *   mask       host, as in lbm_build_tilemap.
  *   pdf_a/b    device, caller-owned, each at least `pdf_bytes` bytes and
  *              256-byte aligned; they must stay allocated until lbm_free.
+ *              With LBM_LAYOUT_TGB, pdf_a is the copy (`pdf_bytes`) and pdf_b
+ *              holds the ghost sets (at least lbm_tiling.ghost_bytes).
  *   rho_init   host, dense nx*ny*nz doubles, or NULL for rho0 everywhere.
  *   u_init     host, dense 3 * nx*ny*nz doubles [component][z][y][x], or
  *              NULL for rest.
@@ -271,6 +285,25 @@ int lbm_moments_batch(lbm_ctx* ctx, lbm_stats* stats, int flags, void* stream);
  * sample's box, NaN at solid nodes; host or device with LBM_OUT_DEVICE).
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_moments_sample(lbm_ctx* ctx, int sample, double* rho, double* u, int flags, void* stream);
+
+/* Period-2 filter for steady-state runs (not in the paper).  Replaces the
+ * current post-collision state by the mean of it and the state one step
+ * earlier (the other PDF copy), word by word in the storage format:
+ * f <- (f(t) + f(t-1)) / 2.
+ *
+ * The BGK step with halfway bounce-back has a slowly damped mode that flips
+ * sign every step (a staggered, checkerboard pattern of the velocity along the
+ * links).  Starts from rest or from a predicted field excite it; a residual
+ * taken over an even number of steps does not see it flip, only its slow decay
+ * (the factor per step is close to -1), so it both delays the test of a
+ * steady state and is still present, at a relative velocity error near 1e-3,
+ * when that test passes.  The mean of two consecutive states removes it and
+ * leaves every slowly varying part of the state, so the fixed point of the
+ * update is unchanged.  Needs at least one lbm_step since lbm_init,
+ * lbm_import_pdfs or the last filter (the other copy must hold the previous
+ * state); applies to every sample of a batch.  Asynchronous on `stream`.
+ * Errors: LBM_ERR_ARG (NULL ctx, no previous state), LBM_ERR_CUDA. */
+int lbm_filter_period2(lbm_ctx* ctx, void* stream);
 
 /* lbm_export_pdfs for sample k of a batch (dense over that sample's box).
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */

@@ -54,6 +54,11 @@ struct lbm_ctx {
     size_t stage_bytes = 0;
     int nblocks = 0;            // blocks of the node kernels (= partial sums)
     bool u_saved_valid = false;
+    bool prev_valid = false;  // the other copy holds the state one step before the current one
+    bool tgb = false;         // LBM_LAYOUT_TGB: pdf[0] is the only copy, pdf[1] the two ghost sets
+    int gset = 0;             // TGB: ghost set written by the last step (read by the next)
+    size_t ghost_set = 0;     // TGB: bytes of one ghost set
+    StepLaunch publish_fn = nullptr;
     std::vector<SampleRange> samples;     // one entry per geometry of a batch
     std::vector<int> part_begin, part_blocks;  // their slices of the partial sums
     StepArgs sa{};
@@ -68,23 +73,45 @@ struct lbm_ctx {
 
 static cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
 
+// The state that alternates every step: the current copy (T2C) or the ghost
+// set (TGB, whose copy never moves).
+static int& parity(lbm_ctx* c) { return c->tgb ? c->gset : c->cur; }
+
+static unsigned char* ghost(lbm_ctx* c, int set) { return static_cast<unsigned char*>(c->pdf[1]) + set * c->ghost_set; }
+
 static int launch_one(lbm_ctx* c, cudaStream_t s) {
     StepArgs a = c->sa;
-    a.src = c->pdf[c->cur];
-    a.dst = c->pdf[1 - c->cur];
+    if (c->tgb) {
+        a.src = a.dst = c->pdf[0];
+        a.ghost_in = ghost(c, c->gset);
+        a.ghost_out = ghost(c, 1 - c->gset);
+    } else {
+        a.src = c->pdf[c->cur];
+        a.dst = c->pdf[1 - c->cur];
+    }
     cudaError_t e = c->step_fn(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-    c->cur = 1 - c->cur;
+    parity(c) = 1 - parity(c);
+    return LBM_OK;
+}
+
+// TGB: fill the current ghost set from the copy (after init or import).
+static int publish_ghosts(lbm_ctx* c, cudaStream_t s) {
+    if (!c->tgb) return LBM_OK;
+    StepArgs a = c->sa;
+    a.src = a.dst = c->pdf[0];
+    a.ghost_out = ghost(c, c->gset);
+    LBM_CUDA_TRY(c->publish_fn(a, s));
     return LBM_OK;
 }
 
 static int build_graph(lbm_ctx* c, int start) {
     LBM_CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    const int saved = c->cur;
-    c->cur = start;
+    const int saved = parity(c);
+    parity(c) = start;
     int rc = LBM_OK;
     for (int k = 0; k < 2 * c->graph_pairs && rc == LBM_OK; k++) rc = launch_one(c, c->cap);
-    c->cur = saved;
+    parity(c) = saved;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap, &g);
     if (rc) {
@@ -145,6 +172,8 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         return fail(LBM_ERR_ARG, "PDF buffers must be 256-byte aligned");
     if (pdf_bytes < T.info.pdf_bytes)
         return fail(LBM_ERR_ARG, "PDF buffers hold %zu bytes, %zu needed", pdf_bytes, T.info.pdf_bytes);
+    if (p->layout != LBM_LAYOUT_T2C && p->layout != LBM_LAYOUT_TGB)
+        return fail(LBM_ERR_ARG, "unknown layout %d", p->layout);
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(LBM_ERR_OOM, "host allocation failed");
@@ -160,12 +189,15 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     const char* env = std::getenv("LBM_NO_GRAPH");
     c->use_graph = !(env && env[0] == '1');
 
-    c->step_fn = select_step(p);
+    c->tgb = p->layout == LBM_LAYOUT_TGB;
+    c->ghost_set = T.info.ghost_bytes / 2;
+    c->step_fn = c->tgb ? select_step_tgb(p) : select_step(p);
+    if (c->tgb) c->publish_fn = select_tgb_publish(p->lattice, p->tile_a, p->storage);
     NodeLaunch init_fn = select_init(p->lattice, p->tile_a, p->model, p->storage);
     c->moments_fn = select_moments(p->lattice, p->tile_a, p->model, p->storage);
     c->export_fn = select_export(p->lattice, p->tile_a, p->storage);
     c->import_fn = select_import(p->lattice, p->tile_a, p->storage);
-    if (!c->step_fn || !init_fn || !c->moments_fn || !c->export_fn || !c->import_fn) {
+    if (!c->step_fn || !init_fn || !c->moments_fn || !c->export_fn || !c->import_fn || (c->tgb && !c->publish_fn)) {
         release(c);
         return fail(LBM_ERR_ARG, "no kernel for lattice %d, tile %d, model %d, storage %d, block %d, persistent %d",
                     p->lattice, p->tile_a, p->model, p->storage, p->block_nodes, p->persistent);
@@ -277,11 +309,19 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         ia.u_in = k == 0 ? d_u : nullptr;
         CTRY(init_fn(ia, s));
     }
-    CTRY(cudaMemsetAsync(pdf_b, 0, T.info.pdf_bytes, s));
+    CTRY(cudaMemsetAsync(pdf_b, 0, c->tgb ? T.info.ghost_bytes : T.info.pdf_bytes, s));
     if (rho_init || u_init) CTRY(cudaStreamSynchronize(s));
 #undef CTRY
 #undef TRY
     c->cur = 0;
+    c->gset = 0;
+    if (c->tgb) {
+        int rc_ = publish_ghosts(c, s);
+        if (rc_) {
+            release(c);
+            return rc_;
+        }
+    }
     *out = c;
     return LBM_OK;
 }
@@ -316,12 +356,13 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps, void* stream) {
     int left = nsteps;
     const int per_graph = 2 * c->graph_pairs;
     if (c->use_graph && left >= per_graph && c->info.n_ftiles > 0) {
-        if (!c->graph[c->cur]) {
-            int rc = build_graph(c, c->cur);
+        const int par = parity(c);
+        if (!c->graph[par]) {
+            int rc = build_graph(c, par);
             if (rc) return rc;
         }
         while (left >= per_graph) {
-            LBM_CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], s));
+            LBM_CUDA_TRY(cudaGraphLaunch(c->graph[par], s));
             left -= per_graph;  // an even number of steps: the current copy is unchanged
         }
     }
@@ -330,6 +371,17 @@ extern "C" int lbm_step(lbm_ctx* c, int nsteps, void* stream) {
         if (rc) return rc;
     }
     c->step += nsteps;
+    if (nsteps > 0) c->prev_valid = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_filter_period2(lbm_ctx* c, void* stream) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+    if (c->tgb) return fail(LBM_ERR_ARG, "the period-2 filter needs the two-copy layout (LBM_LAYOUT_T2C)");
+    if (!c->prev_valid)
+        return fail(LBM_ERR_ARG, "no previous state: step at least once after init, import or a filter");
+    LBM_CUDA_TRY(launch_average(c->pdf[c->cur], c->pdf[1 - c->cur], c->info.pdf_bytes, c->p.storage, S(stream)));
+    c->prev_valid = false;
     return LBM_OK;
 }
 
@@ -523,7 +575,8 @@ extern "C" int lbm_import_pdfs(lbm_ctx* c, const double* pdfs, int64_t step, int
     if (!(flags & LBM_OUT_DEVICE)) LBM_CUDA_TRY(cudaStreamSynchronize(s));
     c->step = step;
     c->u_saved_valid = false;
-    return LBM_OK;
+    c->prev_valid = false;
+    return publish_ghosts(c, s);
 }
 
 extern "C" int lbm_num_samples(const lbm_ctx* c) { return c ? (int)c->samples.size() : 0; }

@@ -96,6 +96,8 @@ struct StepArgs {
     int n_work_blocks;
     const void* src;
     void* dst;
+    const void* ghost_in;  // ghost-buffer form: the set written by the previous step
+    void* ghost_out;       // ghost-buffer form: the set this step writes
     const int32_t* nbr;
     const uint64_t* tmask;
     const long long* tile_off;  // compact layout: PDF block of each tile (in values)
@@ -142,12 +144,16 @@ using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 
 // Kernel selection (nullptr when a combination is not compiled).
 StepLaunch select_step(const lbm_params* p);
+StepLaunch select_step_tgb(const lbm_params* p);
+StepLaunch select_tgb_publish(int lattice, int a, int storage);
+long long tgb_ghost_per_tile(int lattice, int a);
 NodeLaunch select_init(int lattice, int a, int model, int storage);
 NodeLaunch select_moments(int lattice, int a, int model, int storage);
 NodeLaunch select_export(int lattice, int a, int storage);
 NodeLaunch select_import(int lattice, int a, int storage);
 int node_blocks(int lattice, int a, int n_tiles);  // grid of the node kernels
 cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
+cudaError_t launch_average(void* cur, const void* prev, size_t bytes, int storage, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* result, cudaStream_t s);
 
 void fixed_consts(const lbm_params* p, FixedConsts* k);

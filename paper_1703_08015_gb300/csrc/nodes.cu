@@ -190,6 +190,22 @@ __global__ void k_import(const NodeArgs a) {
     });
 }
 
+// cur[k] = (cur[k] + prev[k]) / 2 over the raw words of one PDF copy.
+__global__ void k_average_f64(double* __restrict__ cur, const double* __restrict__ prev, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        cur[k] = __dmul_rn(__dadd_rn(cur[k], prev[k]), 0.5);
+}
+
+__global__ void k_average_f32(float* __restrict__ cur, const float* __restrict__ prev, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        cur[k] = __fmul_rn(__fadd_rn(cur[k], prev[k]), 0.5f);
+}
+
+__global__ void k_average_f16(__half* __restrict__ cur, const __half* __restrict__ prev, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        cur[k] = __float2half_rn(0.5f * (__half2float(cur[k]) + __half2float(prev[k])));
+}
+
 __global__ void k_fill_nan(double* p, size_t n) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
         p[k] = __longlong_as_double(0x7ff8000000000000ll);
@@ -230,6 +246,21 @@ cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const size_t blocks = (n + 255) / 256;
     k_fill_nan<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average(void* cur, const void* prev, size_t bytes, int storage, cudaStream_t s) {
+    const size_t width = storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F16S ? 2 : 4);
+    const size_t n = bytes / width;
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = (n + 255) / 256;
+    const unsigned grid = (unsigned)(blocks < 152 * 64 ? blocks : 152 * 64);
+    if (width == 8)
+        k_average_f64<<<grid, 256, 0, s>>>(static_cast<double*>(cur), static_cast<const double*>(prev), n);
+    else if (width == 4)
+        k_average_f32<<<grid, 256, 0, s>>>(static_cast<float*>(cur), static_cast<const float*>(prev), n);
+    else
+        k_average_f16<<<grid, 256, 0, s>>>(static_cast<__half*>(cur), static_cast<const __half*>(prev), n);
     return cudaGetLastError();
 }
 

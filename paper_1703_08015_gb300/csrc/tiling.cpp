@@ -182,6 +182,7 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     I.nbr_per_tile = T->nn;
     I.n_fluid = n_fluid;
     I.pdf_bytes = (size_t)total * bpv;
+    I.ghost_bytes = p->layout == LBM_LAYOUT_TGB ? 2 * (size_t)count * (size_t)tgb_ghost_per_tile(p->lattice, a) * bpv : 0;
     return LBM_OK;
 }
 
@@ -195,7 +196,7 @@ int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_
     *T = HostTiling{};
     samples->clear();
     long long total_tiles = 0, total_values = 0, total_mesh = 0, total_fluid = 0;
-    size_t total_bytes = 0;
+    size_t total_bytes = 0, total_ghost = 0;
     for (int k = 0; k < n; k++) {
         lbm_params ps = *p;
         ps.nx = dims[3 * k];
@@ -224,6 +225,7 @@ int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_
         total_mesh += S.info.n_tiles;
         total_fluid += S.info.n_fluid;
         total_bytes += S.info.pdf_bytes;
+        total_ghost += S.info.ghost_bytes;
         total_values += (long long)(S.info.pdf_bytes / bytes_per_value(p->storage));
     }
     const int nt = T->d == 3 ? T->a * T->a * T->a : T->a * T->a;
@@ -235,6 +237,7 @@ int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_
     I.nbr_per_tile = T->nn;
     I.n_fluid = total_fluid;
     I.pdf_bytes = total_bytes;
+    I.ghost_bytes = total_ghost;
     return LBM_OK;
 }
 

@@ -23,11 +23,12 @@ LBM_QUASI_COMPRESSIBLE, LBM_INCOMPRESSIBLE = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S, LBM_STORE_F32S = 0, 1, 2, 3
 LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED, LBM_ARITH_FF = 0, 1, 2, 3
 LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
+LBM_LAYOUT_T2C, LBM_LAYOUT_TGB = 0, 1
 
 EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
             "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc",
             "lbm_build_tilemap_batch", "lbm_init_batch", "lbm_moments_batch", "lbm_export_pdfs_sample",
-            "lbm_num_samples", "lbm_moments_sample")
+            "lbm_num_samples", "lbm_moments_sample", "lbm_filter_period2")
 LBM_NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -43,14 +44,14 @@ class lbm_params(ctypes.Structure):
                 ("periodic", ctypes.c_int * 3), ("tau", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("storage", ctypes.c_int),
                 ("arith", ctypes.c_int), ("f16_scale", ctypes.c_double),
-                ("block_nodes", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("block_nodes", ctypes.c_int), ("persistent", ctypes.c_int), ("layout", ctypes.c_int)]
 
 
 class lbm_tiling(ctypes.Structure):
     _fields_ = [("ntx", ctypes.c_int32), ("nty", ctypes.c_int32), ("ntz", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int32), ("n_ftiles", ctypes.c_int32),
                 ("nbr_per_tile", ctypes.c_int32), ("n_fluid", ctypes.c_int64),
-                ("pdf_bytes", ctypes.c_size_t)]
+                ("pdf_bytes", ctypes.c_size_t), ("ghost_bytes", ctypes.c_size_t)]
 
 
 class lbm_stats(ctypes.Structure):
@@ -90,6 +91,7 @@ def library(build: bool = True):
             lib.lbm_export_pdfs_sample.argtypes = [P, I, P, I, P]
             lib.lbm_num_samples.argtypes = [P]
             lib.lbm_moments_sample.argtypes = [P, I, P, P, I, P]
+            lib.lbm_filter_period2.argtypes = [P, P]
             lib.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
                 getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -118,7 +120,8 @@ def lbm_last_error() -> str:
 
 def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0, 0.0, 0.0),
                 rho0=1.0, model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64,
-                arith=LBM_ARITH_AUTO, f16_scale=0.0, block_nodes=0, persistent=0) -> lbm_params:
+                arith=LBM_ARITH_AUTO, f16_scale=0.0, block_nodes=0, persistent=0,
+                layout=LBM_LAYOUT_T2C) -> lbm_params:
     """lbm_params from a mask shape (nz, ny, nx) or (ny, nx)."""
     if len(shape) == 2:
         shape = (1,) + tuple(shape)
@@ -129,7 +132,7 @@ def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0,
         p.periodic[k] = int(bool(periodic[k])) if k < len(periodic) else 0
         p.force[k] = float(force[k]) if k < len(force) else 0.0
     p.tau, p.rho0, p.storage, p.arith, p.f16_scale = float(tau), float(rho0), storage, arith, float(f16_scale)
-    p.block_nodes, p.persistent = int(block_nodes), int(persistent)
+    p.block_nodes, p.persistent, p.layout = int(block_nodes), int(persistent), int(layout)
     return p
 
 
@@ -224,6 +227,10 @@ def lbm_moments_batch(ctx, n_samples, flags=0, stream=None):
     return list(arr), rc
 
 
+def lbm_filter_period2(ctx, stream=None):
+    return _check(library().lbm_filter_period2(ctx, stream))
+
+
 def lbm_moments_sample(ctx, sample, rho=None, u=None, flags=0, stream=None):
     return _check(library().lbm_moments_sample(ctx, int(sample), _ptr(rho), _ptr(u), int(flags), stream))
 
@@ -236,23 +243,33 @@ def lbm_free(ctx):
     return _check(library().lbm_free(ctx))
 
 
+def _pdf_buffers(tiling, layout, device):
+    """The two device buffers lbm_init takes: two PDF copies, or (ghost-buffer
+    layout) the copy and the two ghost sets."""
+    import torch
+
+    a = max(int(tiling.pdf_bytes), 256)
+    b = max(int(tiling.ghost_bytes), 256) if layout == LBM_LAYOUT_TGB else a
+    return [torch.empty(a, dtype=torch.uint8, device=device), torch.empty(b, dtype=torch.uint8, device=device)]
+
+
 class BatchSolver:
     """A batch context (many geometries, one concatenated tile list) plus its
     two PDF copies held as PyTorch device tensors."""
 
     def __init__(self, masks, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
                  model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F32S, arith=LBM_ARITH_AUTO,
-                 f16_scale=0.0, block_nodes=0, persistent=0, device="cuda"):
+                 f16_scale=0.0, block_nodes=0, persistent=0, layout=LBM_LAYOUT_T2C, device="cuda"):
         import torch
 
         self.masks = [np.ascontiguousarray(m[None] if m.ndim == 2 else m, np.uint8) for m in masks]
         self.q = lattice
         self.params = make_params(lattice, self.masks[0].shape, tile_a, periodic, tau, force, rho0, model,
-                                  storage, arith, f16_scale, block_nodes, persistent)
+                                  storage, arith, f16_scale, block_nodes, persistent, layout)
         self.tiling = lbm_build_tilemap_batch(self.params, self.masks)
         nbytes = max(int(self.tiling.pdf_bytes), 256)
         self.device = torch.device(device)
-        self.pdf = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.pdf = _pdf_buffers(self.tiling, layout, self.device)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = lbm_init_batch(self.params, self.masks, self.pdf[0], self.pdf[1], nbytes, self._s())
 
@@ -264,6 +281,9 @@ class BatchSolver:
 
     def stats(self, residual=False):
         return lbm_moments_batch(self.ctx, len(self.masks), LBM_STATS_RESIDUAL if residual else 0, self._s())
+
+    def filter_period2(self):
+        lbm_filter_period2(self.ctx, self._s())
 
     def export_pdfs(self, k):
         out = np.empty((self.q,) + self.masks[k].shape, np.float64)
@@ -287,7 +307,8 @@ class Solver:
 
     def __init__(self, mask, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
                  model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64, arith=LBM_ARITH_AUTO,
-                 f16_scale=0.0, rho_init=None, u_init=None, block_nodes=0, persistent=0, device="cuda"):
+                 f16_scale=0.0, rho_init=None, u_init=None, block_nodes=0, persistent=0,
+                 layout=LBM_LAYOUT_T2C, device="cuda"):
         import torch
 
         self.torch = torch
@@ -298,11 +319,11 @@ class Solver:
         self.shape = self.mask.shape
         self.q = lattice
         self.params = make_params(lattice, self.shape, tile_a, periodic, tau, force, rho0, model, storage,
-                                  arith, f16_scale, block_nodes, persistent)
+                                  arith, f16_scale, block_nodes, persistent, layout)
         self.tiling, _, _ = lbm_build_tilemap(self.params, self.mask, want_map=False, want_nbr=False)
         nbytes = max(int(self.tiling.pdf_bytes), 256)
         self.device = torch.device(device)
-        self.pdf = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.pdf = _pdf_buffers(self.tiling, layout, self.device)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = lbm_init(self.params, self.mask, self.pdf[0], self.pdf[1], nbytes, rho_init, u_init,
                             self._s())
@@ -321,6 +342,9 @@ class Solver:
         st = lbm_stats()
         rc = lbm_moments(self.ctx, rho, u, st, LBM_STATS_RESIDUAL if residual else 0, self._s())
         return rho, u, st, rc
+
+    def filter_period2(self):
+        lbm_filter_period2(self.ctx, self._s())
 
     def stats(self, residual=False):
         st = lbm_stats()

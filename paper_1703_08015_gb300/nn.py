@@ -456,12 +456,14 @@ def sample_geometries(n, seed, side=64, phi=(0.1, 0.6)):
 
 
 def steady_states(masks, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F32S, target=1e-6, check_every=100,
-                  max_steps=150000, batch=64, device="cuda", log=None):
+                  max_steps=150000, batch=64, filter_period2=True, device="cuda", log=None):
     """Runs every geometry to residual < target and returns the steady fields
     as FP32 [n][z][y][x][4] = (rho - 1, u_x, u_y, u_z) on the device, plus the
     per-sample step counts (None where it did not converge).  Geometries are
     batched (one concatenated tile list per batch) in order of fluid fraction,
-    so that each batch holds samples of similar convergence time."""
+    so that each batch holds samples of similar convergence time; with
+    filter_period2 the period-2 mode is removed after every residual check
+    (lbm_filter_period2)."""
     import torch
 
     dev = torch.device(device)
@@ -488,6 +490,8 @@ def steady_states(masks, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F32S, target
                     steps_to[ids[k]] = n
             if all(steps_to[i] is not None for i in ids):
                 break
+            if filter_period2:
+                b.filter_period2()
         for k, i in enumerate(ids):
             lbm.lbm_moments_sample(b.ctx, k, rho, u, lbm.LBM_OUT_DEVICE, b._s())
             lbm_nn_fields_to_target(rho, u, vox, 1.0, 1.0, 1.0, out[i], b._s())
@@ -509,11 +513,37 @@ def inputs_from_masks(masks_dev, force, stream=None):
     return x
 
 
+def augment(x, t, m, code):
+    """One of the 16 symmetries of creeping flow driven along a periodic x
+    axis, applied to a batch (input x [n,z,y,x,2], target t [n,z,y,x,4] =
+    (rho - 1, u_x, u_y, u_z), mask m [n,z,y,x]).  code bit 0: mirror y
+    (u_y -> -u_y); bit 1: mirror z (u_z -> -u_z); bit 2: swap y and z (u_y <->
+    u_z); bit 3: mirror x, which by linearity in the force negates u_y, u_z
+    and rho - 1 and keeps u_x."""
+    sign = [1.0, 1.0, 1.0, 1.0]
+    if code & 1:
+        x, t, m = x.flip(2), t.flip(2), m.flip(2)
+        sign[2] = -sign[2]
+    if code & 2:
+        x, t, m = x.flip(1), t.flip(1), m.flip(1)
+        sign[3] = -sign[3]
+    if code & 4 and x.shape[1] == x.shape[2]:
+        x, t, m = x.transpose(1, 2), t.transpose(1, 2)[..., [0, 1, 3, 2]], m.transpose(1, 2)
+        sign[2], sign[3] = sign[3], sign[2]
+    if code & 8:
+        x, t, m = x.flip(3), t.flip(3), m.flip(3)
+        sign[0], sign[2], sign[3] = -sign[0], -sign[2], -sign[3]
+    if sign != [1.0, 1.0, 1.0, 1.0]:
+        t = t * t.new_tensor(sign)
+    return x.contiguous(), t.contiguous(), m.contiguous()
+
+
 def train(net, masks_dev, fields, force, nu, epochs=20, batch=8, lr=2e-3, lr_min=2e-5, seed=0, log=None,
-          log_every=50):
+          log_every=50, augment_data=True):
     """Adam on the masked mean-squared error of the scaled (rho - 1, u).
     fields: FP32 [n][z][y][x][4] raw steady fields (rho - 1, u) from
-    steady_states().  Fixes the output scales a_rho, a_u from the data.
+    steady_states().  Fixes the output scales a_rho, a_u from the data.  With
+    augment_data every batch is mapped by a random flow symmetry (augment()).
     Returns the loss history [(iteration, loss)]."""
     torch = net.torch
     dev = net.device
@@ -545,6 +575,8 @@ def train(net, masks_dev, fields, force, nu, epochs=20, batch=8, lr=2e-3, lr_min
             xb = x_all.index_select(0, idx)
             tb = tgt.index_select(0, idx)
             mb = masks_dev.index_select(0, idx)
+            if augment_data:
+                xb, tb, mb = augment(xb, tb, mb, int(rng.integers(16)))
             dims = (batch,) + dims_one
             y = net.forward(xb, dims, keep=True)
             dout = torch.empty(y.shape, dtype=torch.bfloat16, device=dev)
@@ -579,12 +611,14 @@ def predict_fields(net, mask, force, nu):
 
 
 def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F64, target=1e-6, check_every=100,
-                   max_steps=60000, device="cuda"):
+                   max_steps=60000, filter_period2=True, device="cuda"):
     """Wall time and steps until the LBM residual (relative change of u over
     check_every steps) falls below target, from rest or from the network's
     prediction; the timed region includes tiling, initialisation and network
-    inference.  Returns a dict (converged, steps, seconds, permeability,
-    velocity field on the fluid nodes)."""
+    inference.  With filter_period2 the state is replaced by the mean of two
+    consecutive states after every residual check that has not converged
+    (lbm_filter_period2).  Returns a dict (converged, steps, seconds,
+    permeability, velocity field on the fluid nodes)."""
     import torch
 
     dev = torch.device(device)
@@ -604,6 +638,8 @@ def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F6
         st, rc = s.stats(residual=True)
         if rc != 0 or st.residual < target:
             break
+        if filter_period2:
+            s.filter_period2()
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     rho, u, _, _ = s.moments()

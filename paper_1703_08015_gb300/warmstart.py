@@ -11,8 +11,9 @@
 3. Adam training of the U-Net in ``nn.py`` with the library's own forward and
    backward kernels.
 4. On the held-out set: time and steps to residual < 1e-6 from rest and from
-   the network's prediction, FP32-storage and FP64 solvers, with the
-   permeability of every converged run against the FP64 zero start.
+   the network's prediction, FP32-storage and FP64 solvers, with and without
+   the period-2 filter (lbm_filter_period2), with the velocity and
+   permeability of every converged run against the filtered FP64 zero start.
 """
 from __future__ import annotations
 
@@ -27,74 +28,78 @@ from . import lbm
 from . import nn
 
 
-def evaluate(net, masks, tau=0.6, force=1e-6, forms=("f32s",), target=1e-6, max_steps=150000, device="cuda",
-             log=None):
-    """Per held-out geometry: zero and warm start for every storage form; the
-    warm start's prediction error against the converged zero-start field."""
-    storages = {"f64": lbm.LBM_STORE_F64, "f32s": lbm.LBM_STORE_F32S, "f32": lbm.LBM_STORE_F32,
-                "f16s": lbm.LBM_STORE_F16S}
+STORAGES = {"f64": lbm.LBM_STORE_F64, "f32s": lbm.LBM_STORE_F32S, "f32": lbm.LBM_STORE_F32,
+            "f16s": lbm.LBM_STORE_F16S}
+# (label, storage, start, period-2 filter); the first is the baseline
+CASES_FULL = [("f64_zero_plain", "f64", "zero", False), ("f64_zero", "f64", "zero", True),
+              ("f64_warm", "f64", "warm", True), ("f32s_zero", "f32s", "zero", True),
+              ("f32s_warm", "f32s", "warm", True), ("f32s_warm_plain", "f32s", "warm", False)]
+CASES_F32S = [("f32s_zero", "f32s", "zero", True), ("f32s_warm", "f32s", "warm", True)]
+
+
+def evaluate(net, masks, cases, tau=0.6, force=1e-6, target=1e-6, max_steps=150000, device="cuda", log=None):
+    """Per held-out geometry and case: steps and wall time to residual < target
+    (tiling, initialisation and network inference included), permeability,
+    and the velocity error of the converged field and of the prediction
+    against the first filtered zero start (the most accurate field)."""
     nu = (tau - 0.5) / 3.0
     rows = []
     for k, m in enumerate(masks):
         row = {"fluid_fraction": float(m.mean())}
         fl = m.astype(bool)
-        u_ref = None
-        for form in forms:
-            for start, model in (("zero", None), ("warm", net)):
-                r = nn.solve_to_steady(m, model, tau=tau, force=force, storage=storages[form], target=target,
-                                       max_steps=max_steps, device=device)
-                u = r.pop("u")
-                if form == forms[0] and start == "zero":
-                    u_ref = u
-                row[f"{form}_{start}"] = r
+        fields = {}
+        for label, form, start, filt in cases:
+            r = nn.solve_to_steady(m, net if start == "warm" else None, tau=tau, force=force,
+                                   storage=STORAGES[form], target=target, max_steps=max_steps,
+                                   filter_period2=filt, device=device)
+            fields[label] = r.pop("u")
+            row[label] = r
+        ref_label = next(lb for lb, _, st, f in cases if st == "zero" and f)
+        u_ref, k_ref = fields[ref_label], row[ref_label]["permeability"]
+        nrm = float(np.sqrt(np.sum(u_ref * u_ref)))
+        for label in fields:
+            d = fields[label] - u_ref
+            row[label]["u_rel_err"] = float(np.sqrt(np.sum(d * d))) / nrm
+            row[label]["permeability_rel_err"] = abs(row[label]["permeability"] / k_ref - 1.0)
         _, u_pred = nn.predict_fields(net, m, force, nu)
         d = u_pred[:, fl] - u_ref
-        row["prediction_u_rel_l2"] = float(np.sqrt(np.sum(d * d) / np.sum(u_ref * u_ref)))
+        row["prediction_u_rel_l2"] = float(np.sqrt(np.sum(d * d))) / nrm
         k_pred = nu * float(np.sum(u_pred[0][fl])) / m.size / force
-        k_ref = row[f"{forms[0]}_zero"]["permeability"]
         row["prediction_permeability_rel_err"] = abs(k_pred / k_ref - 1.0)
-        for form in forms:
-            for start in ("zero", "warm"):
-                r = row[f"{form}_{start}"]
-                for base in {f"{form}_zero", f"{forms[0]}_zero"}:
-                    r["permeability_rel_err_vs_" + base] = abs(r["permeability"] / row[base]["permeability"] - 1.0)
         rows.append(row)
         if log:
-            s = ", ".join(f"{f}: {row[f + '_zero']['steps']} -> {row[f + '_warm']['steps']} steps" for f in forms)
+            s = ", ".join(f"{lb} {row[lb]['steps']}" for lb, *_ in cases)
             log(f"held-out {k + 1}/{len(masks)} fluid {row['fluid_fraction']:.2f}: {s}; "
                 f"prediction error u {row['prediction_u_rel_l2']:.3f}")
     return rows
 
 
-def summarize(rows, forms):
-    out = {}
-    base = "f64_zero" if "f64" in forms else f"{forms[0]}_zero"
-    for form in forms:
-        ok = [r for r in rows if r[f"{form}_zero"]["converged"] and r[f"{form}_warm"]["converged"]]
-        if not ok:
-            continue
-        sr = np.array([r[f"{form}_warm"]["steps"] / r[f"{form}_zero"]["steps"] for r in ok])
-        tr = np.array([r[f"{form}_warm"]["seconds"] / r[f"{form}_zero"]["seconds"] for r in ok])
-        tz = sum(r[f"{form}_zero"]["seconds"] for r in ok)
-        tw = sum(r[f"{form}_warm"]["seconds"] for r in ok)
-        out[form] = {
-            "geometries": len(ok),
-            "zero_start_not_converged": sum(not r[f"{form}_zero"]["converged"] for r in rows),
-            "warm_start_fallbacks": sum(bool(r[f"{form}_warm"].get("fallback")) for r in rows),
-            "steps_ratio_median": float(np.median(sr)), "steps_ratio_mean": float(sr.mean()),
-            "time_ratio_median": float(np.median(tr)),
-            "total_seconds_zero": tz, "total_seconds_warm": tw, "speedup_total": tz / tw,
-            "warm_faster_fraction": float(np.mean(tr < 1.0)),
-            "max_permeability_rel_err_warm_vs_" + base: max(r[f"{form}_warm"]["permeability_rel_err_vs_" + base]
-                                                            for r in ok),
-        }
-    if "f64" in forms:
-        ok = [r for r in rows if r["f64_zero"]["converged"]]
-        for form in forms:
-            for start in ("zero", "warm"):
-                key = f"{form}_{start}"
-                t = sum(r[key]["seconds"] for r in ok)
-                out.setdefault("vs_f64_zero", {})[key] = sum(r["f64_zero"]["seconds"] for r in ok) / t
+def summarize(rows, cases):
+    """Per case: geometries converged, median steps, total time over the
+    geometries where every case converged, speedups against the first case
+    and against the filtered zero start of the same storage."""
+    labels = [lb for lb, *_ in cases]
+    ok = [r for r in rows if all(r[lb]["converged"] for lb in labels)]
+    out = {"geometries": len(rows), "all_converged": len(ok)}
+    if not ok:
+        return out
+    tot = {lb: sum(r[lb]["seconds"] for r in ok) for lb in labels}
+    for lb, form, start, filt in cases:
+        steps = np.array([r[lb]["steps"] for r in ok])
+        e = {"converged": sum(r[lb]["converged"] for r in rows), "steps_median": float(np.median(steps)),
+             "steps_mean": float(steps.mean()), "seconds_total": tot[lb],
+             "speedup_vs_" + labels[0]: tot[labels[0]] / tot[lb],
+             "u_rel_err_median": float(np.median([r[lb]["u_rel_err"] for r in ok])),
+             "permeability_rel_err_max": max(r[lb]["permeability_rel_err"] for r in ok),
+             "fallbacks": sum(bool(r[lb].get("fallback")) for r in rows)}
+        zero = f"{form}_zero"
+        if start == "warm" and zero in labels:
+            ratio = np.array([r[lb]["steps"] / r[zero]["steps"] for r in ok])
+            e["steps_ratio_vs_" + zero + "_median"] = float(np.median(ratio))
+            e["speedup_vs_" + zero] = tot[zero] / tot[lb]
+            e["faster_than_" + zero + "_fraction"] = float(np.mean([r[lb]["seconds"] < r[zero]["seconds"]
+                                                                     for r in ok]))
+        out[lb] = e
     out["prediction_u_rel_l2_median"] = float(np.median([r["prediction_u_rel_l2"] for r in rows]))
     out["prediction_permeability_rel_err_median"] = float(np.median([r["prediction_permeability_rel_err"]
                                                                      for r in rows]))
@@ -155,12 +160,11 @@ def main(argv=None):
         log(f"saved {args.out}")
     held, _ = nn.sample_geometries(args.n_heldout, args.seed_heldout, args.side)
     n64 = min(args.n_heldout_f64, len(held))
-    rows = evaluate(net, held[:n64], args.tau, args.force, forms=("f64", "f32s"), max_steps=args.max_steps,
-                    device=dev, log=log)
-    rows += evaluate(net, held[n64:], args.tau, args.force, forms=("f32s",), max_steps=args.max_steps, device=dev,
+    rows = evaluate(net, held[:n64], CASES_FULL, args.tau, args.force, max_steps=args.max_steps, device=dev, log=log)
+    rows += evaluate(net, held[n64:], CASES_F32S, args.tau, args.force, max_steps=args.max_steps, device=dev,
                      log=log)
-    report["heldout_f64_and_f32s"] = summarize(rows[:n64], ("f64", "f32s"))
-    report["heldout_f32s"] = summarize(rows, ("f32s",))
+    report["heldout_all_cases"] = summarize(rows[:n64], CASES_FULL)
+    report["heldout_f32s"] = summarize(rows, CASES_F32S)
     report["rows"] = rows
     log(json.dumps({k: v for k, v in report.items() if k.startswith("heldout")}))
     if args.report:

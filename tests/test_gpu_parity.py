@@ -218,3 +218,106 @@ def test_residual_decreases_towards_steady_state():
         res.append(st.residual)
     s.close()
     assert all(b < a for a, b in zip(res, res[1:]))
+
+
+def test_filter_period2_is_the_mean_of_consecutive_states(oracle):
+    """lbm_filter_period2 replaces the state by the mean of the current and
+    the previous post-collision state: bit-exact against the mean of the two
+    exported FP64 states, and within the 1e-12 bar against the oracle's."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(24, 22, 18), seed=12, r_min=2, r_max=4, target_fluid=0.45)
+    per, tau, F = (1, 0, 0), 0.6, (1e-5, 0, 0)
+    s = lbm.Solver(mask, 19, 4, per, tau, F)
+    try:
+        with pytest.raises(lbm.LBMError):  # no previous state right after init
+            s.filter_period2()
+        s.step(299)
+        a = s.export_pdfs()
+        s.step(1)
+        b = s.export_pdfs()
+        s.filter_period2()
+        c = s.export_pdfs()
+        with pytest.raises(lbm.LBMError):  # the previous copy is spent
+            s.filter_period2()
+        s.step(1)
+        s.filter_period2()
+    finally:
+        s.close()
+    fl = mask.astype(bool)
+    assert np.array_equal(c[:, fl], 0.5 * (a[:, fl] + b[:, fl]))
+    fa = oracle.run(19, mask, per, tau, F, oracle.init(19, mask), 299)
+    fb = oracle.run(19, mask, per, tau, F, fa, 1)
+    assert max_rel(c, 0.5 * (fa + fb), mask) <= TOL
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_STORE_F32S, lbm.LBM_STORE_F16S], ids=["f32s", "f16s"])
+def test_filter_period2_reduced_storage(storage):
+    """In the reduced storage forms the mean is taken on the stored deviations
+    (one rounding in the storage format)."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(24, 22, 18), seed=12, r_min=2, r_max=4, target_fluid=0.45)
+    s = lbm.Solver(mask, 19, 4, (1, 0, 0), 0.6, (1e-5, 0, 0), storage=storage)
+    try:
+        s.step(200)
+        a = s.export_pdfs()
+        s.step(1)
+        b = s.export_pdfs()
+        s.filter_period2()
+        c = s.export_pdfs()
+    finally:
+        s.close()
+    fl = mask.astype(bool)
+    w = np.array(lbm_weights())[:, None]
+    da, db, dc = a[:, fl] - w, b[:, fl] - w, c[:, fl] - w
+    want = 0.5 * (da + db)
+    # the export adds the stored deviation to w_i in FP64, which rounds tiny
+    # deviations to the ulp of w_i (about 7e-18): that is the absolute floor
+    ulp, tiny = (2.0 ** -23, 2e-17) if storage == lbm.LBM_STORE_F32S else (2.0 ** -10, 1e-12)
+    tol = ulp * np.maximum(np.abs(da), np.abs(db)) + tiny
+    bad = np.abs(dc - want) > tol
+    k = np.unravel_index(np.argmax(np.abs(dc - want) / tol), dc.shape)
+    assert not bad.any(), (int(bad.sum()), k, da[k], db[k], dc[k], want[k])
+
+
+def lbm_weights():
+    return [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+
+
+def test_filter_period2_shortens_the_run_to_steady_state():
+    """Zero start on a small sphere pack: with the filter after every residual
+    check the run reaches residual < 1e-6 in far fewer steps, and lands closer
+    to the long-run steady state than the plain run does when its residual
+    test passes."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(32, seed=11, r_min=3, r_max=6, target_fluid=0.45)
+    fl = mask.astype(bool)
+
+    def solve(filt, max_steps=40000, extra=0):
+        s = lbm.Solver(mask, 19, 4, (1, 0, 0), 0.6, (1e-6, 0, 0))
+        try:
+            s.stats(residual=True)
+            n = 0
+            while n < max_steps:
+                s.step(100)
+                n += 100
+                st, _ = s.stats(residual=True)
+                if st.residual < 1e-6:
+                    break
+                if filt:
+                    s.filter_period2()
+            for _ in range(extra):  # reference: keep filtering and stepping
+                s.step(1000)
+                s.filter_period2()
+                s.step(100)
+            u = s.moments()[1]
+        finally:
+            s.close()
+        return n, u[:, fl]
+
+    n_plain, u_plain = solve(False)
+    n_filt, u_filt = solve(True)
+    _, u_ref = solve(True, extra=20)
+    err = lambda u: float(np.sqrt(np.sum((u - u_ref) ** 2) / np.sum(u_ref ** 2)))
+    assert n_filt < 0.3 * n_plain, (n_filt, n_plain)
+    assert err(u_filt) < 1e-5
+    assert err(u_filt) < 0.1 * err(u_plain)

@@ -129,3 +129,37 @@ def test_unet_gradients_by_finite_differences():
         bm[0] -= h
         fd = (loss({**params, name: (w, bp)}) - loss({**params, name: (w, bm)})) / (2 * h)
         assert fd == pytest.approx(grads[name][1][0], rel=1e-5, abs=1e-7), name
+
+
+def test_flow_symmetries_map_steady_states_to_steady_states():
+    """The augmentation symmetries map a steady LBM solution (from the oracle,
+    creeping flow along a periodic x axis) to the steady solution of the
+    transformed geometry."""
+    torch = pytest.importorskip("torch")
+    import oracle as O
+    from paper_1703_08015_gb300 import geometry as geo
+    from paper_1703_08015_gb300.nn import augment
+
+    mask, _ = geo.sphere_pack_3d(12, seed=3, r_min=2, r_max=3.5, target_fluid=0.55)
+    per, tau, F = (1, 0, 0), 0.7, (1e-6, 0, 0)
+
+    def steady(m):
+        f = O.init(19, m)
+        for _ in range(6):
+            f = O.run(19, m, per, tau, F, f, 600)
+            f = 0.5 * (f + O.run(19, m, per, tau, F, f, 1))  # two-state mean removes the period-2 mode
+        rho, u = O.moments(19, m, per, F, f)[:2]
+        t = np.stack([rho - 1, u[0], u[1], u[2]], axis=-1)
+        return np.where(m[..., None] > 0, t, 0.0)
+
+    t0 = steady(mask)
+    scale = np.abs(t0).max(axis=(0, 1, 2))  # per channel
+    # mirrors in y, z and the y/z swap are exact symmetries of the lattice update;
+    # the x mirror holds for creeping flow (reversibility), here to ~1e-4
+    for code, tol in ((1, 1e-8), (2, 1e-8), (4, 1e-8), (7, 1e-8), (8, 1e-3), (15, 1e-3)):
+        x = torch.zeros((1,) + mask.shape + (2,))
+        xt, tt, mt = augment(x, torch.from_numpy(t0[None]), torch.from_numpy(mask[None]), code)
+        m2 = mt[0].numpy().astype(np.uint8)
+        want = steady(m2)
+        got = tt[0].numpy()
+        assert np.all(np.max(np.abs(got - want), axis=(0, 1, 2)) < tol * scale), code
