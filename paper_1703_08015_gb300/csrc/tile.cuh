@@ -98,6 +98,42 @@ __device__ __forceinline__ NodePos<(1 << TL::LA)> node_pos(int node) {
     return p;
 }
 
+// Per node, once: for each axis and each link component c in {-1, 0, +1}
+// (index c + 1), the source coordinate (r - c) mod A already shifted into the
+// node index, and the step to the neighbour slot (in slot units of that axis)
+// when r - c leaves the tile.
+template <class L, int A>
+struct PullBase {
+    using TL = Tile<L, A>;
+    int nx[3], ny[3], nz[3];  // shifted source coordinates
+    int tx[3], ty[3], tz[3];  // slot steps: 1, 3, 9 per tile along x, y, z
+    __device__ __forceinline__ PullBase(const NodePos<A>& p) {
+        nx[0] = (p.lx + 1) & (A - 1);
+        nx[1] = p.lx;
+        nx[2] = (p.lx - 1) & (A - 1);
+        ny[0] = ((p.ly + 1) & (A - 1)) << TL::LA;
+        ny[1] = p.ly << TL::LA;
+        ny[2] = ((p.ly - 1) & (A - 1)) << TL::LA;
+        tx[0] = p.lx == A - 1;
+        tx[1] = 0;
+        tx[2] = -(p.lx == 0);
+        ty[0] = 3 * (p.ly == A - 1);
+        ty[1] = 0;
+        ty[2] = -3 * (p.ly == 0);
+        if (TL::D == 3) {
+            nz[0] = ((p.lz + 1) & (A - 1)) << (2 * TL::LA);
+            nz[1] = p.lz << (2 * TL::LA);
+            nz[2] = ((p.lz - 1) & (A - 1)) << (2 * TL::LA);
+            tz[0] = 9 * (p.lz == A - 1);
+            tz[1] = 0;
+            tz[2] = -9 * (p.lz == 0);
+        } else {
+            nz[0] = nz[1] = nz[2] = 0;
+            tz[0] = tz[1] = tz[2] = 0;
+        }
+    }
+};
+
 // Source of the pull along link I: the neighbour slot and node index that
 // hold r - c_I.
 template <class L, int A, int I>
@@ -105,6 +141,10 @@ struct PullSource {
     using TL = Tile<L, A>;
     using K = Link<L, I>;
     int slot, sn;
+    __device__ __forceinline__ PullSource(const PullBase<L, A>& b) {
+        slot = TL::CENTER + b.tx[K::cx + 1] + b.ty[K::cy + 1] + b.tz[K::cz + 1];
+        sn = b.nx[K::cx + 1] | b.ny[K::cy + 1] | b.nz[K::cz + 1];
+    }
     __device__ __forceinline__ PullSource(const NodePos<A>& p) {
         const int sx = p.lx - K::cx, sy = p.ly - K::cy, sz = p.lz - K::cz;
         const int tx = K::cx > 0 ? -(sx < 0) : (K::cx < 0 ? (sx >= A) : 0);
@@ -125,13 +165,15 @@ __device__ __forceinline__ int gather(const NeighShared<Tile<L, A>, TPB>& sh, in
     const int own_stride = sh.stride[lt][TL::CENTER];
     const int own_rank = fluid_rank<TL::W>(sh.m[lt][TL::CENTER], node);
     f[0] = __ldg(own + own_rank);
+    const T* own_r = own + own_rank;  // bounce-back sources: own_r + opp * own_stride
+    const PullBase<L, A> pb(p);
     static_for<1, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const PullSource<L, A, i> s(p);
+        const PullSource<L, A, i> s(pb);
         bool fl;
         const int r = fluid_bit_rank<TL::W>(sh.m[lt][s.slot], s.sn, fl);
         const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * sh.stride[lt][s.slot] + r
-                          : own + Link<L, i>::opp * own_stride + own_rank;
+                          : own_r + Link<L, i>::opp * own_stride;
         f[i] = __ldg(src);
     });
     return own_rank;
