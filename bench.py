@@ -283,7 +283,8 @@ def run_ours(args):
     s_d = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2}[args.storage]
     bytes_per_launch = n_fluid * pm.B_node(lat, s_d)
     achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
-    traffic, tnote = committed_traffic(args.workload, arith_name)
+    traffic, tnote = (committed_traffic(args.workload, arith_name if args.storage == "f64" else args.storage)
+                      if args.layout == "t2c" else (None, None))
     dev_bytes = int(tiling.pdf_bytes) + (int(tiling.ghost_bytes) if args.layout == "tgb" else int(tiling.pdf_bytes))
     tiling_stats = {"n_ftiles": int(tiling.n_ftiles), "n_tiles": int(tiling.n_tiles),
                     "phi": n_fluid / mask.size,

@@ -257,6 +257,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.f16_inv_scale = c->p.f16_scale > 0 ? 1.0 / c->p.f16_scale : 0.0;
     sa.omega_f = (float)sa.omega;
     for (int k = 0; k < 3; k++) sa.force_f[k] = (float)sa.force[k];
+    f32_consts(&c->p, sa.omega, sa.force, &sa.f32c);
     sa.f16_scale_f = (float)sa.f16_scale;
     sa.f16_inv_scale_f = (float)sa.f16_inv_scale;
     sa.err = c->d_err;

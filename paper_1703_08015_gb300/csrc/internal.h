@@ -90,6 +90,16 @@ struct FFConsts {      // u_c = 1 / ulp(w_c): class quantities in ulps of w_c
     float2 so[19];     // 3 (1 - w/2) w_i (c_i.F) u_c
 };
 
+// Constants of the FP32 collision (reduced storage forms), per weight class c
+// and per link i.
+struct F32Consts {
+    float keep;      // 1 - w
+    float ow[3];     // w * w_c
+    float kw3[3];    // 3 (1 - w/2) w_c
+    float be[19];    // 9 (1 - w/2) w_i (c_i.F)
+    float so[19];    // 3 (1 - w/2) w_i (c_i.F)
+};
+
 struct StepArgs {
     const WorkBlock* blocks;  // [n_work_blocks]
     const uint32_t* nodes;    // fluid-node list: tile * NT + node
@@ -112,6 +122,7 @@ struct StepArgs {
     int* err;             // device error word (0 = none)
     FixedConsts fx;
     FFConsts ffc;
+    F32Consts f32c;
 };
 
 struct NodeArgs {         // kernels that visit every node of every tile
@@ -144,6 +155,7 @@ using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 
 // Kernel selection (nullptr when a combination is not compiled).
 StepLaunch select_step(const lbm_params* p);
+void f32_consts(const lbm_params* p, double omega, const double* force, F32Consts* k);
 StepLaunch select_step_tgb(const lbm_params* p);
 StepLaunch select_tgb_publish(int lattice, int a, int storage);
 long long tgb_ghost_per_tile(int lattice, int a);

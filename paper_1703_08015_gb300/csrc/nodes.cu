@@ -67,9 +67,8 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
     const int node = threadIdx.x - lt * TL::NT;
     const int tile = a.tile_begin + blockIdx.x * TPB + lt;
     const int tile_end = a.tile_begin + a.n_tiles;
-    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, a.tile_off, a.tile_stride,
-                                 static_cast<const unsigned char*>(a.pdf), (int)sizeof(T), tile_end, tile, lt,
-                                 node);
+    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, a.tile_off, a.tile_stride, a.tile_begin + blockIdx.x * TPB,
+                                 tile_end, tile, lt, node);
     __syncthreads();
     double acc[kStats];
 #pragma unroll
@@ -79,7 +78,7 @@ __global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs 
     const bool want_fields = a.rho_out || a.u_out;
     if (tile < tile_end && mask_bit(sh, lt, TL::CENTER, node) && (!want_fields || dense_index<L, A>(a, tile, p, n))) {
         T raw[L::Q];
-        gather<L, A, TPB, T>(sh, lt, node, p, raw);
+        gather<L, A, TPB, T>(sh, a.pdf, lt, node, p, raw);
         double f[L::Q];
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;

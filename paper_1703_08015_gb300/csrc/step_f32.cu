@@ -24,19 +24,18 @@ __global__ void __launch_bounds__(BT) k_step_f32(const StepArgs a) {
     // one work block per thread block, or (persistent) a grid-stride loop over them
     for (int wbi = blockIdx.x; wbi < a.n_work_blocks; wbi += PERSIST ? (int)gridDim.x : a.n_work_blocks) {
         WorkNode wn;
-        if (stage_work_at<TL, work_tiles()>(sh, a, (int)sizeof(T), wbi, wn)) {
+        if (stage_work_at<TL, work_tiles()>(sh, a, wbi, wn)) {
             const NodePos<A> p = node_pos<TL>(wn.node);
             T raw[L::Q];
-            const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
-            const int stride = sh.stride[wn.lt][TL::CENTER];
+            const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, raw);
+            const int stride = sh.loc[wn.lt][TL::CENTER].y;
             float g[L::Q];
             static_for<0, L::Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 g[i] = IO::template dev<i>(raw[i], a);
             });
-            collide_f32<L, MODEL>(g, a.omega_f, a.force_f);
-            T* out = static_cast<T*>(a.dst) +
-                     (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+            collide_f32<L, MODEL>(g, a.f32c, a.force_f);
+            T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
             static_for<0, L::Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 out[i * stride] = IO::template raw<i>(g[i], a);
@@ -88,6 +87,31 @@ static StepLaunch pick_storage(int model, int storage, int block_nodes, int pers
     if (storage == LBM_STORE_F16S) return pick<L, A, StoreF16S>(model, block_nodes, persistent);
     if (storage == LBM_STORE_F32S) return pick<L, A, StoreF32S>(model, block_nodes, persistent);
     return nullptr;
+}
+
+template <class L>
+static void f32_consts_for(double omega, const double* force, F32Consts* k) {
+    const double kf = 1.0 - 0.5 * omega;
+    const double F[3] = {force[0], force[1], L::D == 3 ? force[2] : 0.0};
+    k->keep = (float)(1.0 - omega);
+    for (int c = 0; c < 3; c++) {
+        k->ow[c] = (float)(omega * L::wc_[c]);
+        k->kw3[c] = (float)(3.0 * kf * L::wc_[c]);
+    }
+    for (int i = 0; i < L::Q; i++) {
+        const double cF = L::cx_[i] * F[0] + L::cy_[i] * F[1] + L::cz_[i] * F[2];
+        const double w = L::wc_[L::cls_[i]];
+        k->be[i] = (float)(9.0 * kf * w * cF);
+        k->so[i] = (float)(3.0 * kf * w * cF);
+    }
+}
+
+void f32_consts(const lbm_params* p, double omega, const double* force, F32Consts* k) {
+    *k = F32Consts{};
+    if (p->lattice == LBM_D2Q9)
+        f32_consts_for<D2Q9>(omega, force, k);
+    else if (p->lattice == LBM_D3Q19)
+        f32_consts_for<D3Q19>(omega, force, k);
 }
 
 StepLaunch select_step_f32(int lattice, int a, int model, int storage, int block_nodes, int persistent) {

@@ -12,19 +12,18 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_f64(const StepArg
     using T = typename S::T;
     __shared__ NeighShared<TL, work_tiles()> sh;
     WorkNode wn;
-    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    if (!stage_work<TL, work_tiles()>(sh, a, wn)) return;
     const NodePos<A> p = node_pos<TL>(wn.node);
     T raw[L::Q];
-    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, raw);
-    const int stride = sh.stride[wn.lt][TL::CENTER];
+    const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, raw);
+    const int stride = sh.loc[wn.lt][TL::CENTER].y;
     double f[L::Q];
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         f[i] = S::template to_f64<L, i>(raw[i], a.f16_inv_scale);
     });
     collide_f64<L, MODEL>(f, a.omega, a.force);
-    T* out = static_cast<T*>(a.dst) +
-             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+    T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     static_for<0, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         out[i * stride] = S::template from_f64<L, i>(f[i], a.f16_scale);

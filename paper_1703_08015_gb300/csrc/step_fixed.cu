@@ -176,16 +176,15 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_fixed(const
     using T = unsigned long long;
     __shared__ NeighShared<TL, work_tiles()> sh;
     WorkNode wn;
-    if (!stage_work<TL, work_tiles()>(sh, a, (int)sizeof(T), wn)) return;
+    if (!stage_work<TL, work_tiles()>(sh, a, wn)) return;
     const NodePos<A> p = node_pos<TL>(wn.node);
     T b[L::Q];
-    const int rank = gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
-    const int stride = sh.stride[wn.lt][TL::CENTER];
-    T* out = static_cast<T*>(a.dst) +
-             (reinterpret_cast<const T*>(sh.base[wn.lt][TL::CENTER]) - static_cast<const T*>(a.src)) + rank;
+    const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
+    const int stride = sh.loc[wn.lt][TL::CENTER].y;
+    T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_fixed<L, MODEL>(b, a.fx, out, stride)) {
         // out of the fixed-point range: the same update with FP64 instructions
-        gather<L, A, work_tiles(), T>(sh, wn.lt, wn.node, p, b);
+        gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
         double f[L::Q];
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;

@@ -99,12 +99,12 @@ constexpr int ghost_per_tile() {
 // when it is outside, bounce-back when the source is not a fluid node.
 template <class L, int A, int KMAX, class T>
 __device__ __forceinline__ int gather_tgb(const NeighShared<Tile<L, A>, KMAX>& sh, const int (&nbt)[KMAX][Tile<L, A>::NN],
-                                          const T* __restrict__ ghost_in, int lt, int node, const NodePos<A>& p,
-                                          T (&f)[L::Q]) {
+                                          const T* copy, const T* __restrict__ ghost_in, int lt, int node,
+                                          const NodePos<A>& p, T (&f)[L::Q]) {
     using TL = Tile<L, A>;
     constexpr int E = ghost_per_tile<L, A>();
-    const T* own = reinterpret_cast<const T*>(sh.base[lt][TL::CENTER]);
-    const int own_stride = sh.stride[lt][TL::CENTER];
+    const T* own = copy + sh.origin + sh.loc[lt][TL::CENTER].x;
+    const int own_stride = sh.loc[lt][TL::CENTER].y;
     const int own_rank = fluid_rank<TL::W>(sh.m[lt][TL::CENTER], node);
     f[0] = own[own_rank];
     static_for<1, L::Q>([&](auto I) {
@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
     __shared__ int nbt[work_tiles()][TL::NN];
     const WorkBlock wb = a.blocks[blockIdx.x];
     T* copy = static_cast<T*>(a.dst);  // the single copy (src == dst)
+    const long long origin = __ldg(a.tile_off + wb.tile_begin);
+    if (threadIdx.x == 0) sh.origin = origin;
     for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
         const int lt = k / (TL::NN * TL::W);
         const int r = k - lt * (TL::NN * TL::W);
@@ -145,8 +147,8 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
         const int nb = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
         sh.m[lt][slot][w] = nb >= 0 ? __ldg(a.tmask + (size_t)nb * TL::W + w) : 0ull;
         if (w == 0) {
-            sh.base[lt][slot] = reinterpret_cast<const unsigned char*>(copy + (nb >= 0 ? __ldg(a.tile_off + nb) : 0ll));
-            sh.stride[lt][slot] = nb >= 0 ? __ldg(a.tile_stride + nb) : 0;
+            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(a.tile_off + nb) - origin), __ldg(a.tile_stride + nb))
+                                       : make_int2(0, 0);
             nbt[lt][slot] = nb;
         }
     }
@@ -162,12 +164,12 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
         lt = tile - wb.tile_begin;
         p = node_pos<TL>(node);
         T raw[L::Q];
-        rank = gather_tgb<L, A, work_tiles(), T>(sh, nbt, static_cast<const T*>(a.ghost_in), lt, node, p, raw);
+        rank = gather_tgb<L, A, work_tiles(), T>(sh, nbt, copy, static_cast<const T*>(a.ghost_in), lt, node, p, raw);
         if constexpr (ARITH == 0) {
             using IO = F32Io<L, S>;
             float g[L::Q];
             static_for<0, L::Q>([&](auto I) { g[decltype(I)::value] = IO::template dev<decltype(I)::value>(raw[decltype(I)::value], a); });
-            collide_f32<L, MODEL>(g, a.omega_f, a.force_f);
+            collide_f32<L, MODEL>(g, a.f32c, a.force_f);
             static_for<0, L::Q>([&](auto I) { vals[decltype(I)::value] = IO::template raw<decltype(I)::value>(g[decltype(I)::value], a); });
         } else {
             bool done = false;
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
     }
     __syncthreads();  // every read of this block's tiles is done: update in place
     if (active) {
-        T* own = const_cast<T*>(reinterpret_cast<const T*>(sh.base[lt][TL::CENTER]));
-        const int stride = sh.stride[lt][TL::CENTER];
+        T* own = copy + sh.origin + sh.loc[lt][TL::CENTER].x;
+        const int stride = sh.loc[lt][TL::CENTER].y;
         T* gout = static_cast<T*>(a.ghost_out) + (size_t)tile * E;
         static_for<0, L::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;

@@ -18,11 +18,14 @@
 
 namespace lbm {
 
+// The neighbourhood of the tiles of one block.  PDF blocks are addressed from
+// the block's origin (the compact offset of its first tile) with 32-bit value
+// offsets; the tiling checks that every neighbour lies within 2^30 values.
 template <class TL, int TPB>
 struct NeighShared {
-    const unsigned char* base[TPB][TL::NN];  // PDF block of each neighbour slot
-    int stride[TPB][TL::NN];                 // its values per link
-    uint64_t m[TPB][TL::NN][TL::W];          // its fluid-node bits (0 when removed)
+    int2 loc[TPB][TL::NN];           // x: the slot's PDF block, values from the origin; y: values per link
+    uint64_t m[TPB][TL::NN][TL::W];  // its fluid-node bits (0 when removed)
+    long long origin;                // compact offset of the block's first tile (values)
 };
 
 // Rank of node n among the fluid nodes of a tile (its slot in the compact
@@ -45,16 +48,16 @@ __device__ __forceinline__ void stage_neighbourhood(NeighShared<TL, TPB>& sh, co
                                                     const uint64_t* __restrict__ tmask,
                                                     const long long* __restrict__ tile_off,
                                                     const int32_t* __restrict__ tile_stride,
-                                                    const unsigned char* pdf, int value_bytes, int n_tiles,
-                                                    int tile, int lt, int node) {
+                                                    int first_tile, int n_tiles, int tile, int lt, int node) {
+    const long long origin = __ldg(tile_off + first_tile);
+    if (lt == 0 && node == 0) sh.origin = origin;
     for (int k = node; k < TL::NN * TL::W; k += TL::NT) {
         const int slot = k / TL::W, w = k - slot * TL::W;
         const int nb = tile < n_tiles ? __ldg(nbr + (size_t)tile * TL::NN + slot) : -1;
         sh.m[lt][slot][w] = nb >= 0 ? __ldg(tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0) {
-            sh.base[lt][slot] = pdf + (nb >= 0 ? __ldg(tile_off + nb) : 0ll) * value_bytes;
-            sh.stride[lt][slot] = nb >= 0 ? __ldg(tile_stride + nb) : 0;
-        }
+        if (w == 0)
+            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(tile_off + nb) - origin), __ldg(tile_stride + nb))
+                                       : make_int2(0, 0);
     }
 }
 
@@ -158,25 +161,31 @@ struct PullSource {
 // Gather the q post-collision words that arrive at `node` (raw storage words)
 // from the compact blocks; returns the node's own slot (its fluid rank).
 template <class L, int A, int TPB, class T>
-__device__ __forceinline__ int gather(const NeighShared<Tile<L, A>, TPB>& sh, int lt, int node,
+__device__ __forceinline__ int gather(const NeighShared<Tile<L, A>, TPB>& sh, const void* pdf, int lt, int node,
                                       const NodePos<A>& p, T (&f)[L::Q]) {
     using TL = Tile<L, A>;
-    const T* own = reinterpret_cast<const T*>(sh.base[lt][TL::CENTER]);
-    const int own_stride = sh.stride[lt][TL::CENTER];
+    const T* org = static_cast<const T*>(pdf) + sh.origin;
+    const int2 own = sh.loc[lt][TL::CENTER];
     const int own_rank = fluid_rank<TL::W>(sh.m[lt][TL::CENTER], node);
-    f[0] = __ldg(own + own_rank);
-    const T* own_r = own + own_rank;  // bounce-back sources: own_r + opp * own_stride
+    const int own_r = own.x + own_rank;  // bounce-back sources: own_r + opp * own.y
+    f[0] = __ldg(org + own_r);
     const PullBase<L, A> pb(p);
     static_for<1, L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const PullSource<L, A, i> s(pb);
         bool fl;
         const int r = fluid_bit_rank<TL::W>(sh.m[lt][s.slot], s.sn, fl);
-        const T* src = fl ? reinterpret_cast<const T*>(sh.base[lt][s.slot]) + i * sh.stride[lt][s.slot] + r
-                          : own_r + Link<L, i>::opp * own_stride;
-        f[i] = __ldg(src);
+        const int2 nb = sh.loc[lt][s.slot];
+        const int idx = fl ? nb.x + i * nb.y + r : own_r + Link<L, i>::opp * own.y;
+        f[i] = __ldg(org + idx);
     });
     return own_rank;
+}
+
+// The node's own values in a copy laid out like the source: base + i * stride.
+template <class TL, int TPB, class T>
+__device__ __forceinline__ T* own_slot(const NeighShared<TL, TPB>& sh, void* pdf, int lt, int rank) {
+    return static_cast<T*>(pdf) + sh.origin + sh.loc[lt][TL::CENTER].x + rank;
 }
 
 // ---- storage policies: raw words <-> FP64 values ------------------------------
@@ -249,20 +258,20 @@ struct WorkNode {
 // fluid node.  Every thread of the block must call it (it holds the barrier);
 // returns false for threads beyond the block's node count.
 template <class TL, int KMAX>
-__device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
-                                              int wbi, WorkNode& wn) {
+__device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int wbi,
+                                              WorkNode& wn) {
     const WorkBlock wb = a.blocks[wbi];
-    const unsigned char* pdf = static_cast<const unsigned char*>(a.src);
+    const long long origin = __ldg(a.tile_off + wb.tile_begin);
+    if (threadIdx.x == 0) sh.origin = origin;
     for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
         const int lt = k / (TL::NN * TL::W);
         const int r = k - lt * (TL::NN * TL::W);
         const int slot = r / TL::W, w = r - slot * TL::W;
         const int nb = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
         sh.m[lt][slot][w] = nb >= 0 ? __ldg(a.tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0) {
-            sh.base[lt][slot] = pdf + (nb >= 0 ? __ldg(a.tile_off + nb) : 0ll) * value_bytes;
-            sh.stride[lt][slot] = nb >= 0 ? __ldg(a.tile_stride + nb) : 0;
-        }
+        if (w == 0)
+            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(a.tile_off + nb) - origin), __ldg(a.tile_stride + nb))
+                                       : make_int2(0, 0);
     }
     __syncthreads();  // the only barrier of the step (Fig. 5)
     if ((int)threadIdx.x >= wb.count) return false;
@@ -274,9 +283,8 @@ __device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const S
 }
 
 template <class TL, int KMAX>
-__device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, int value_bytes,
-                                           WorkNode& wn) {
-    return stage_work_at<TL, KMAX>(sh, a, value_bytes, blockIdx.x, wn);
+__device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, WorkNode& wn) {
+    return stage_work_at<TL, KMAX>(sh, a, blockIdx.x, wn);
 }
 
 }  // namespace lbm

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -172,6 +173,15 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
         T->tile_stride[k] = stride;
         total += (long long)lattice_q(p->lattice) * stride;
     }
+
+    // the step kernels address a tile's neighbours with 32-bit value offsets
+    // from the first tile of their block: neighbours must lie within 2^30 values
+    for (int32_t k = 0; k < count; k++)
+        for (int slot = 0; slot < T->nn; slot++) {
+            const int32_t nb = T->nbr[(size_t)k * T->nn + slot];
+            if (nb >= 0 && std::llabs(T->tile_off[nb] - T->tile_off[k]) > (1ll << 30))
+                return fail(LBM_ERR_CAPACITY, "neighbour tiles lie more than 2^30 values apart (tile plane too large)");
+        }
 
     lbm_tiling& I = T->info;
     I.ntx = ntx;

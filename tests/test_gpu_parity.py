@@ -270,9 +270,10 @@ def test_filter_period2_reduced_storage(storage):
     w = np.array(lbm_weights())[:, None]
     da, db, dc = a[:, fl] - w, b[:, fl] - w, c[:, fl] - w
     want = 0.5 * (da + db)
-    # the export adds the stored deviation to w_i in FP64, which rounds tiny
-    # deviations to the ulp of w_i (about 7e-18): that is the absolute floor
-    ulp, tiny = (2.0 ** -23, 2e-17) if storage == lbm.LBM_STORE_F32S else (2.0 ** -10, 1e-12)
+    # the export adds the stored deviation to w_i in FP64, which rounds each of
+    # the three exported states to half an ulp of w_i: one ulp of w_0 = 1/3
+    # (5.6e-17) is the absolute floor
+    ulp, tiny = (2.0 ** -23, 6e-17) if storage == lbm.LBM_STORE_F32S else (2.0 ** -10, 1e-12)
     tol = ulp * np.maximum(np.abs(da), np.abs(db)) + tiny
     bad = np.abs(dc - want) > tol
     k = np.unravel_index(np.argmax(np.abs(dc - want) / tol), dc.shape)
