@@ -16,7 +16,7 @@
 namespace lbm {
 
 template <class L, int A, int MODEL, class S, int BT, bool PERSIST>
-__global__ void __launch_bounds__(BT) k_step_f32(const StepArgs a) {
+__global__ void __launch_bounds__(BT, (!PERSIST && BT <= 256) ? 1536 / BT : 1) k_step_f32(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
     using IO = F32Io<L, S>;
