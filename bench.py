@@ -60,6 +60,19 @@ def parse():
     return ap.parse_args()
 
 
+def replica_throughput(ms, n_fluid, steps, world, device):
+    """Whole-job throughput of `world` independent replicas (one per GPU, each
+    updating n_fluid nodes `steps` times): the slowest rank's time over all
+    ranks' updates.  Returns (max time in ms, MLUPS)."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, n_fluid * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -115,16 +128,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-STEP_SOURCES = ("internal.h", "lattice.cuh", "tile.cuh", "collide_f64.cuh", "step_ff.cu", "step_fixed.cu",
-                "step_f64.cu", "step_f32.cu", "tiling.cpp")
+STEP_SOURCES = {  # the sources each step kernel is built from
+    "common": ("internal.h", "lattice.cuh", "tile.cuh", "tiling.cpp"),
+    "ff": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
+    "fixed": ("collide_f64.cuh", "step_fixed.cu"),
+    "f64": ("collide_f64.cuh", "step_f64.cu"),
+    "f32": ("collide_f32.cuh", "step_f32.cu"),
+}
 
 
-def kernel_source_sha():
-    """Hash of the sources the step kernels are built from (a committed traffic
+def kernel_source_sha(kind="ff"):
+    """Hash of the sources a step kernel is built from (a committed traffic
     figure is used only while they are unchanged)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1703_08015_gb300", "csrc")
-    for f in STEP_SOURCES:
+    for f in STEP_SOURCES["common"] + STEP_SOURCES[kind]:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -139,7 +157,8 @@ def committed_traffic(workload, arith):
     with open(path) as f:
         d = json.load(f)
     e = d.get(f"{workload}:{arith}")
-    if not e or e.get("kernel_source_sha") != kernel_source_sha():
+    kind = arith if arith in STEP_SOURCES else "f32"
+    if not e or e.get("kernel_source_sha") != kernel_source_sha(kind):
         return None, None
     return e.get("dram_bytes_per_launch"), e.get("note")
 
@@ -261,11 +280,7 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
     step_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
-    ms_all = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_all, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_all.item())
-    value = n_fluid * args.steps * world / (ms_max * 1e-3) / 1e6
+    ms_max, value = replica_throughput(ms, n_fluid, args.steps, world, dev)
     arith_name = {lbm.LBM_ARITH_AUTO: "ff", lbm.LBM_ARITH_FIXED: "fixed", lbm.LBM_ARITH_F64: "f64",
                   lbm.LBM_ARITH_FF: "ff"}[arith]
     tiling = solver.tiling
