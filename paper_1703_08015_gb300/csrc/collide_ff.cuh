@@ -108,7 +108,9 @@ __device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
 
 // FP64 bit pattern of w + r ulp(w) with r the integer within one unit of
 // x = x.h + x.l (units of ulp(w)): x.h splits exactly into hi 2^24 + rem, and
-// rem and x.l are rounded to integers separately.
+// rem and x.l are rounded to integers separately.  (A single FP32 -> int64
+// conversion of x.h is slower here: those conversions issue at a fraction of
+// the 32-bit rate.)
 __device__ __forceinline__ unsigned long long ulp_round(ff x, unsigned long long wb, bool& ok) {
     ok &= fabsf(x.h) < pow2f(47) && fabsf(x.l) < pow2f(30);
     const int hi = __float2int_rz(__fmul_rn(x.h, pow2f(-24)));            // |hi| < 2^23
