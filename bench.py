@@ -60,6 +60,26 @@ def parse():
     return ap.parse_args()
 
 
+ISSUE_PEAK = 152 * 4 * 2.07e9  # warp instructions per second: SMs x schedulers x 1/clock x max SM clock
+
+
+def issue_roofline(args, arith_name, n_fluid, step_ms):
+    """Instruction-issue view of the step kernel (the FP64 and FP32 steps are
+    bound by issue and latency, not by HBM): warp instructions per launch from
+    the committed ncu count per fluid node, over the measured kernel time,
+    against one instruction per scheduler per clock."""
+    if args.layout != "t2c":
+        return None
+    e = committed_profile(args.workload, arith_name if args.storage == "f64" else args.storage)
+    per_node = e.get("warp_instructions_per_node")
+    if not per_node:
+        return None
+    achieved = per_node * n_fluid / (step_ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp instructions/s",
+            "frac": achieved / ISSUE_PEAK, "warp_instructions_per_node": per_node,
+            "peak_source": "152 SMs x 4 schedulers x 1 instruction/clock x 2.07 GHz"}
+
+
 def replica_throughput(ms, n_fluid, steps, world, device):
     """Whole-job throughput of `world` independent replicas (one per GPU, each
     updating n_fluid nodes `steps` times): the slowest rank's time over all
@@ -146,6 +166,20 @@ def kernel_source_sha(kind="ff"):
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
+
+
+def committed_profile(workload, arith):
+    """The committed ncu figures of the step kernel for this workload, if they
+    were taken on the current kernel sources (else {})."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        e = json.load(f).get(f"{workload}:{arith}")
+    kind = arith if arith in STEP_SOURCES else "f32"
+    if not e or e.get("kernel_source_sha") != kernel_source_sha(kind):
+        return {}
+    return e
 
 
 def committed_traffic(workload, arith):
@@ -327,6 +361,7 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel": "k_step (tiled stream+collide)", "bytes_per_launch": bytes_per_launch,
                      "step_kernel_ms": step_ms, "traffic_note": tnote},
+        "issue_roofline": issue_roofline(args, arith_name, n_fluid, step_ms),
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,
