@@ -37,18 +37,9 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const St
     const int stride = sh.loc[wn.lt][TL::CENTER].y;
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
-        // out of range: the same update with FP64 instructions
-        gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
-        double f[L::Q];
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            f[i] = __longlong_as_double((long long)b[i]);
-        });
-        collide_f64<L, MODEL>(f, a.omega, a.force);
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            out[i * stride] = (T)__double_as_longlong(f[i]);
-        });
+        // out of range: listed for the FP64 fallback kernel that follows this one
+        const unsigned k = atomicAdd(a.fb_count, 1u);
+        if (k < a.fb_cap) a.fb_list[k] = (uint32_t)wn.tile * TL::NT + wn.node;
     }
 }
 

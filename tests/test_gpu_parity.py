@@ -322,3 +322,28 @@ def test_filter_period2_shortens_the_run_to_steady_state():
     assert n_filt < 0.3 * n_plain, (n_filt, n_plain)
     assert err(u_filt) < 1e-5
     assert err(u_filt) < 0.1 * err(u_plain)
+
+
+@pytest.mark.parametrize("arith", [lbm.LBM_ARITH_FF, lbm.LBM_ARITH_FIXED], ids=["ff", "fixed"])
+def test_fp64_fallback_far_from_equilibrium(oracle, arith):
+    """A start far from equilibrium (velocity ramping from 0 to 0.02 along y)
+    sends most nodes out of the float-float / fixed-point range (|f_i - w_i|
+    beyond about w_i / 32, |u| > ~0.006); they are listed and updated by the
+    native-FP64 fallback kernel, the rest by the fast path, and the whole
+    state still meets the 1e-12 bar."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(24, 22, 18), seed=12, r_min=2, r_max=4, target_fluid=0.55)
+    nz, ny, nx = mask.shape
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = (0.02 * np.arange(ny) / (ny - 1))[None, :, None]
+    u[1] = 0.003 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, None, :]
+    rho = 1.0 + 0.001 * np.cos(2 * np.pi * np.arange(nz) / nz)[:, None, None] * np.ones((nz, ny, nx))
+    per, tau, F, steps = (1, 0, 0), 0.7, (1e-5, 0, 0), 30
+    s = lbm.Solver(mask, 19, 4, per, tau, F, arith=arith, rho_init=rho, u_init=u)
+    try:
+        s.step(steps)
+        gpu = s.export_pdfs()
+    finally:
+        s.close()
+    ref = oracle.run(19, mask, per, tau, F, oracle.init(19, mask, rho=rho, u=u), steps)
+    assert max_rel(gpu, ref, mask) <= TOL
