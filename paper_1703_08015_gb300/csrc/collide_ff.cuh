@@ -89,6 +89,19 @@ __device__ __forceinline__ bool small_ll(long long x, int log2bound) {
     return (unsigned long long)(x + (1ll << log2bound)) < (2ull << log2bound);
 }
 
+// -2^47 <= x < 2^47, from the high word alone.
+__device__ __forceinline__ bool within_2p47(long long x) {
+    return (unsigned)((int)(x >> 32) + (1 << 15)) < (1u << 16);
+}
+
+// Distance from w to the nearer edge of its binade [2^e, 2^(e+1)), in ulps of w.
+constexpr double ulps_to_binade_edge(double w) {
+    const int e = fp_exp(w);
+    const double lo = e >= 0 ? pow2f(e) : 1.0 / (double)pow2f(-e), ulp = lo / 4503599627370496.0;  // 2^52
+    const double d = (w - lo) < (2.0 * lo - w) ? (w - lo) : (2.0 * lo - w);
+    return d / ulp;
+}
+
 // A value x * 2^-60 (|x| < 2^57) as float-float, exactly up to the last piece.
 __device__ __forceinline__ ff q60_to_ff(long long x) {
     const float f2 = __fmul_rn(__int2float_rn((int)(x >> 48)), pow2f(-12));
@@ -111,14 +124,16 @@ __device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
 // rem and x.l are rounded to integers separately.  (A single FP32 -> int64
 // conversion of x.h is slower here: those conversions issue at a fraction of
 // the 32-bit rate.)
+//
+// The result stays in the binade of w (same sign and exponent bits): |r| <
+// 2^47 + 2^30 + 1 ulps, and every lattice weight lies at least 2^48 ulps from
+// the edges of its binade (checked at compile time in collide_ff).
 __device__ __forceinline__ unsigned long long ulp_round(ff x, unsigned long long wb, bool& ok) {
     ok &= fabsf(x.h) < pow2f(47) && fabsf(x.l) < pow2f(30);
     const int hi = __float2int_rz(__fmul_rn(x.h, pow2f(-24)));            // |hi| < 2^23
     const float rem = __fmaf_rn(__int2float_rn(hi), -pow2f(24), x.h);     // exact, |rem| < 2^24
     const int lo = __float2int_rn(rem) + __float2int_rn(x.l);
-    const unsigned long long out = wb + (unsigned long long)(((long long)hi << 24) + (long long)lo);
-    ok &= ((out ^ wb) >> 52) == 0;  // same sign and binade as w
-    return out;
+    return wb + (unsigned long long)(((long long)hi << 24) + (long long)lo);
 }
 
 template <class L, int C>
@@ -132,12 +147,16 @@ template <class L, int MODEL>
 __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], const FixedConsts& k,
                                            const FFConsts& c, unsigned long long* out, int stride) {
     constexpr int Q = L::Q;
+    static_assert(ulps_to_binade_edge(L::wc_[0]) >= 281474976710656.0 &&
+                      ulps_to_binade_edge(L::wc_[1]) >= 281474976710656.0 &&
+                      ulps_to_binade_edge(L::wc_[2]) >= 281474976710656.0,
+                  "a weight within 2^48 ulps of its binade edge: ulp_round would need its binade check");
     long long d[Q];
     bool ok = true;
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         d[i] = (long long)(b[i] - (unsigned long long)k.w_bits[Link<L, i>::cls]);
-        ok &= small_ll(d[i], 47);  // also rejects another binade, sign, NaN/Inf
+        ok &= within_2p47(d[i]);  // also rejects another binade, sign, NaN/Inf
     });
     // exact sums per class (units of ulp(w_c)), then one shift per class to 2^-60
     long long sr[3] = {0, 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};

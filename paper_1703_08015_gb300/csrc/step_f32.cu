@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(BT, (!PERSIST && BT <= 256) ? 1536 / BT : 1) k
     // one work block per thread block, or (persistent) a grid-stride loop over them
     for (int wbi = blockIdx.x; wbi < a.n_work_blocks; wbi += PERSIST ? (int)gridDim.x : a.n_work_blocks) {
         WorkNode wn;
-        if (stage_work_at<TL, work_tiles()>(sh, a, wbi, wn)) {
+        if (stage_work_at<TL, work_tiles(), BT>(sh, a, wbi, wn)) {
             const NodePos<A> p = node_pos<TL>(wn.node);
             T raw[L::Q];
             const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, raw);

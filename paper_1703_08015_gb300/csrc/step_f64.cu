@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_f64(const StepArg
     using T = typename S::T;
     __shared__ NeighShared<TL, work_tiles()> sh;
     WorkNode wn;
-    if (!stage_work<TL, work_tiles()>(sh, a, wn)) return;
+    if (!stage_work<TL, work_tiles(), work_threads<L, A>()>(sh, a, wn)) return;
     const NodePos<A> p = node_pos<TL>(wn.node);
     T raw[L::Q];
     const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, raw);

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const St
     using T = unsigned long long;
     __shared__ NeighShared<TL, work_tiles()> sh;
     WorkNode wn;
-    if (!stage_work<TL, work_tiles()>(sh, a, wn)) return;
+    if (!stage_work<TL, work_tiles(), work_threads<L, A>()>(sh, a, wn)) return;
     const NodePos<A> p = node_pos<TL>(wn.node);
     T b[L::Q];
     const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
@@ -38,8 +38,9 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const St
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
         // out of range: listed for the FP64 fallback kernel that follows this one
+        // (the node's list entry is read again rather than kept live)
         const unsigned k = atomicAdd(a.fb_count, 1u);
-        if (k < a.fb_cap) a.fb_list[k] = (uint32_t)wn.tile * TL::NT + wn.node;
+        if (k < a.fb_cap) a.fb_list[k] = __ldg(a.nodes + a.blocks[blockIdx.x].node_begin + threadIdx.x);
     }
 }
 

@@ -257,22 +257,58 @@ struct WorkNode {
 // Stage the neighbourhoods of the block's tiles, then decode this thread's
 // fluid node.  Every thread of the block must call it (it holds the barrier);
 // returns false for threads beyond the block's node count.
-template <class TL, int KMAX>
+// The block's BT threads copy the neighbourhoods of work block `wb`'s tiles
+// into `sh` (visible to the block after the next barrier).  The entries a
+// thread copies are unrolled so that the loads of all of them are in flight
+// together: one round trip for the neighbour indices, one for what they point
+// at, whatever the number of entries per thread.
+template <class TL, int KMAX, int BT>
+__device__ __forceinline__ void stage_tables(NeighShared<TL, KMAX>& sh, const StepArgs& a, const WorkBlock& wb) {
+    constexpr int PER_TILE = TL::NN * TL::W;
+    constexpr int R = (KMAX * PER_TILE + BT - 1) / BT;  // entries per thread, at most
+    const long long origin = __ldg(a.tile_off + wb.tile_begin);
+    if (threadIdx.x == 0) sh.origin = origin;
+    const int total = wb.n_tiles * PER_TILE;
+    int nb[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int k = (int)threadIdx.x + r * BT;
+        nb[r] = -1;
+        if (k < total) {
+            const int lt = k / PER_TILE, slot = (k - lt * PER_TILE) / TL::W;
+            nb[r] = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
+        }
+    }
+    uint64_t m[R];
+    int2 loc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int k = (int)threadIdx.x + r * BT;
+        const int w = k % TL::W;
+        m[r] = 0ull;
+        loc[r] = make_int2(0, 0);
+        if (nb[r] >= 0) {
+            m[r] = __ldg(a.tmask + (size_t)nb[r] * TL::W + w);
+            if (w == 0) loc[r] = make_int2((int)(__ldg(a.tile_off + nb[r]) - origin), __ldg(a.tile_stride + nb[r]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int k = (int)threadIdx.x + r * BT;
+        if (k < total) {
+            const int lt = k / PER_TILE, rem = k - lt * PER_TILE;
+            const int slot = rem / TL::W, w = rem - slot * TL::W;
+            sh.m[lt][slot][w] = m[r];
+            if (w == 0) sh.loc[lt][slot] = loc[r];
+        }
+    }
+}
+
+template <class TL, int KMAX, int BT>
 __device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int wbi,
                                               WorkNode& wn) {
     const WorkBlock wb = a.blocks[wbi];
-    const long long origin = __ldg(a.tile_off + wb.tile_begin);
-    if (threadIdx.x == 0) sh.origin = origin;
-    for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
-        const int lt = k / (TL::NN * TL::W);
-        const int r = k - lt * (TL::NN * TL::W);
-        const int slot = r / TL::W, w = r - slot * TL::W;
-        const int nb = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
-        sh.m[lt][slot][w] = nb >= 0 ? __ldg(a.tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0)
-            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(a.tile_off + nb) - origin), __ldg(a.tile_stride + nb))
-                                       : make_int2(0, 0);
-    }
+    stage_tables<TL, KMAX, BT>(sh, a, wb);
     __syncthreads();  // the only barrier of the step (Fig. 5)
     if ((int)threadIdx.x >= wb.count) return false;
     const uint32_t e = __ldg(a.nodes + wb.node_begin + threadIdx.x);
@@ -282,9 +318,9 @@ __device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const S
     return true;
 }
 
-template <class TL, int KMAX>
+template <class TL, int KMAX, int BT>
 __device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const StepArgs& a, WorkNode& wn) {
-    return stage_work_at<TL, KMAX>(sh, a, blockIdx.x, wn);
+    return stage_work_at<TL, KMAX, BT>(sh, a, blockIdx.x, wn);
 }
 
 }  // namespace lbm
