@@ -46,6 +46,7 @@ struct lbm_ctx {
     WorkBlock* d_blocks = nullptr;
     long long* d_tile_off = nullptr;
     int32_t* d_tile_stride = nullptr;
+    ulonglong2* d_tinfo = nullptr;  // packed per-tile record of the step kernels' staging
     double* d_partials = nullptr;
     double* d_result = nullptr;
     double* d_u_saved = nullptr;
@@ -144,6 +145,7 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_blocks);
     cudaFree(c->d_tile_off);
     cudaFree(c->d_tile_stride);
+    cudaFree(c->d_tinfo);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_u_saved);
@@ -244,6 +246,19 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
     TRY(upload(&c->d_tile_stride, T.tile_stride, s));
+    {
+        // one 16-byte load per neighbour slot when the step kernels stage a neighbourhood
+        std::vector<ulonglong2> rec((size_t)nf);
+        for (int k = 0; k < nf; k++) {
+            const long long off = T.tile_off[k];
+            const int32_t st = T.tile_stride[k];
+            if (off < 0 || off >= (1ll << 40) || st < 0 || st >= (1 << 24))
+                TRY(fail(LBM_ERR_CAPACITY, "tile offset or stride beyond the packed tile record"));
+            rec[k].x = T.tmask[(size_t)k * T.words];
+            rec[k].y = ((unsigned long long)off << 24) | (unsigned long long)st;
+        }
+        TRY(upload(&c->d_tinfo, rec, s));
+    }
     CTRY(cudaMalloc(&c->d_partials, (size_t)n_partials * 8 * sizeof(double)));
     CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double) * samples.size()));
     CTRY(cudaMalloc(&c->d_err, sizeof(int)));
@@ -272,6 +287,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.tmask = c->d_tmask;
     sa.tile_off = c->d_tile_off;
     sa.tile_stride = c->d_tile_stride;
+    sa.tinfo = c->d_tinfo;
     sa.n_tiles = nf;
     sa.tau = p->tau;
     sa.omega = 1.0 / p->tau;

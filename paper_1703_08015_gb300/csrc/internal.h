@@ -112,6 +112,7 @@ struct StepArgs {
     const uint64_t* tmask;
     const long long* tile_off;  // compact layout: PDF block of each tile (in values)
     const int32_t* tile_stride; // compact layout: values per link of each tile
+    const ulonglong2* tinfo;    // per tile, one 16-byte record: {first fluid-mask word, tile_off << 24 | tile_stride}
     int n_tiles;
     double omega;         // 1 / tau
     double tau;

@@ -288,8 +288,13 @@ __device__ __forceinline__ void stage_tables(NeighShared<TL, KMAX>& sh, const St
         m[r] = 0ull;
         loc[r] = make_int2(0, 0);
         if (nb[r] >= 0) {
-            m[r] = __ldg(a.tmask + (size_t)nb[r] * TL::W + w);
-            if (w == 0) loc[r] = make_int2((int)(__ldg(a.tile_off + nb[r]) - origin), __ldg(a.tile_stride + nb[r]));
+            if (w == 0) {  // mask word 0, offset and stride in one record
+                const ulonglong2 t = __ldg(a.tinfo + nb[r]);
+                m[r] = t.x;
+                loc[r] = make_int2((int)((long long)(t.y >> 24) - origin), (int)(t.y & 0xFFFFFFull));
+            } else {
+                m[r] = __ldg(a.tmask + (size_t)nb[r] * TL::W + w);
+            }
         }
     }
 #pragma unroll
@@ -308,10 +313,11 @@ template <class TL, int KMAX, int BT>
 __device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int wbi,
                                               WorkNode& wn) {
     const WorkBlock wb = a.blocks[wbi];
+    const bool active = (int)threadIdx.x < wb.count;
+    const uint32_t e = active ? __ldg(a.nodes + wb.node_begin + threadIdx.x) : 0u;  // in flight during the staging
     stage_tables<TL, KMAX, BT>(sh, a, wb);
     __syncthreads();  // the only barrier of the step (Fig. 5)
-    if ((int)threadIdx.x >= wb.count) return false;
-    const uint32_t e = __ldg(a.nodes + wb.node_begin + threadIdx.x);
+    if (!active) return false;
     wn.tile = (int)(e >> (TL::D * TL::LA));
     wn.node = (int)(e & (TL::NT - 1));
     wn.lt = wn.tile - wb.tile_begin;
