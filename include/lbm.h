@@ -223,8 +223,8 @@ int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
                     void* stream);
 
 /* Largest number of partial-sum blocks lbm_stats_noalloc can hold: its
- * static scratch is LBM_NOALLOC_MAX_BLOCKS * 8 doubles (4 MiB) per GPU. */
-#define LBM_NOALLOC_MAX_BLOCKS 65536
+ * static scratch is LBM_NOALLOC_MAX_BLOCKS * 8 doubles (512 KiB) per GPU. */
+#define LBM_NOALLOC_MAX_BLOCKS 8192
 
 /* The mass and momentum sums of lbm_moments without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that
@@ -240,8 +240,8 @@ int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
  *              to the host and the stream is not synchronised).
  * The per-block partial sums go to a file-scope device array of
  * LBM_NOALLOC_MAX_BLOCKS * 8 doubles that every GPU loading the library
- * keeps until the process exits.  One partial block covers 4 non-empty
- * tiles of 4^3 or 8^2 nodes, or one tile of 8^3, 16^2 or 32^2 nodes, so
+ * keeps until the process exits.  One partial block covers 32 non-empty
+ * tiles of 4^3 or 8^2 nodes, or 8 tiles of 8^3, 16^2 or 32^2 nodes, so
  * tilings that need more than LBM_NOALLOC_MAX_BLOCKS blocks (more than
  * 262,144 non-empty 4^3 tiles, for example) are rejected with
  * LBM_ERR_CAPACITY.  The

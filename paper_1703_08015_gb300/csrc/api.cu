@@ -49,7 +49,7 @@ struct lbm_ctx {
     ulonglong2* d_tinfo = nullptr;  // packed per-tile record of the step kernels' staging
     double* d_partials = nullptr;
     double* d_result = nullptr;
-    double* d_u_saved = nullptr;
+    float2* d_u_saved = nullptr;
     int* d_err = nullptr;
     double* d_stage = nullptr;  // dense staging for host outputs
     size_t stage_bytes = 0;
@@ -309,6 +309,8 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     na.coords = c->d_coords;
     na.tile_off = c->d_tile_off;
     na.tile_stride = c->d_tile_stride;
+    na.tinfo = c->d_tinfo;
+    na.n_slots = (long long)(T.info.pdf_bytes / (bytes_per_value(p->storage) * (size_t)lattice_q(p->lattice)));
     na.tile_begin = 0;
     na.n_tiles = nf;
     na.nx = samples[0].nx;
@@ -441,7 +443,7 @@ static NodeArgs sample_args(const lbm_ctx* c, size_t k) {
 // a fixed order into d_result[8k .. 8k+7].
 static int launch_sample_moments(lbm_ctx* c, double* d_rho, double* d_u, bool residual, cudaStream_t s) {
     if (residual && !c->d_u_saved)
-        LBM_CUDA_TRY(cudaMalloc(&c->d_u_saved, (size_t)c->info.n_ftiles * 3 * c->nt * sizeof(double) + 8));
+        LBM_CUDA_TRY(cudaMalloc(&c->d_u_saved, (size_t)c->na.n_slots * 3 * sizeof(float2) + 8));
     for (size_t k = 0; k < c->samples.size(); k++) {
         NodeArgs a = sample_args(c, k);
         a.rho_out = d_rho;

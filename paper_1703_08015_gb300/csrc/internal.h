@@ -150,7 +150,9 @@ struct NodeArgs {         // kernels that visit every node of every tile
     double* u_out;            // dense [3][N] or NULL
     double* dense_pdf;        // dense [q][N]
     const double* dense_pdf_in;
-    double* u_saved;          // [n_tiles][3][NT] or NULL
+    const ulonglong2* tinfo;  // per tile: {first fluid-mask word, tile_off << 24 | tile_stride}
+    long long n_slots;        // fluid-node slots of one link (values of a PDF copy / q)
+    float2* u_saved;          // [3][n_slots] velocity of the last residual check (float-float) or NULL
     int residual;             // compare and save velocity
     double* partials;         // [blocks][8]
 };
@@ -169,7 +171,7 @@ NodeLaunch select_init(int lattice, int a, int model, int storage);
 NodeLaunch select_moments(int lattice, int a, int model, int storage);
 NodeLaunch select_export(int lattice, int a, int storage);
 NodeLaunch select_import(int lattice, int a, int storage);
-int node_blocks(int lattice, int a, int n_tiles);  // grid of the node kernels
+int node_blocks(int lattice, int a, int n_tiles);  // grid (= partial sums) of the moments kernel
 cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
 cudaError_t launch_average(void* cur, const void* prev, size_t bytes, int storage, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* result, cudaStream_t s);

@@ -3,12 +3,12 @@
 // of the PDFs.  None of them is on the per-step path.
 #include <cmath>
 
-#include "collide_f64.cuh"
-#include "tile.cuh"
+#include "collide_ff.cuh"
 
 namespace lbm {
 
 constexpr int kStats = 8;  // mass, momentum x/y/z, |u|^2, |u - u_saved|^2, fluid count, spare
+constexpr int kMomentGroups = 8;  // tile groups per block of the moments kernel
 
 template <class L, int A>
 __device__ __forceinline__ bool dense_index(const NodeArgs& a, int tile, const NodePos<A>& p, size_t& n) {
@@ -56,68 +56,260 @@ __global__ void k_init(const NodeArgs a) {
 }
 
 // ---- moments and reductions ---------------------------------------------------------
+// The moments (Eq. 5; Eq. 6 for the incompressible model) of every fluid node
+// are formed without FP64 instructions, which GB300 issues at a small
+// fraction of its FP32 rate: FP64 words in the exact range of the float-float
+// step give rho - 1 and j as exact integer sums (units of 2^-60), every other
+// form sums its deviations f_i - w_i in float-float; u = (j + F/2) / rho
+// follows in float-float.  A node whose FP64 words fall outside that range
+// (or are not finite) takes the FP64 formulas.  Each thread accumulates its
+// nodes of kMomentGroups tile groups in float-float, and the block sums its
+// threads in a fixed order; the per-block partials are FP64.
+
+__device__ __forceinline__ ff ff_of(double v) {
+    const float h = __double2float_rn(v);
+    return ff{h, __double2float_rn(v - (double)h)};
+}
+__device__ __forceinline__ double dbl_of(ff x) { return (double)x.h + (double)x.l; }
+
+// x + y for a float y, low part not renormalised (callers renormalise once).
+__device__ __forceinline__ ff ff_acc(ff x, float y) {
+    const ff s = two_sum(x.h, y);
+    return ff{s.h, __fadd_rn(x.l, s.l)};
+}
+__device__ __forceinline__ ff ff_norm(ff x) { return fast2(x.h, x.l); }
+
+template <class L>
+constexpr long long q60_weight_excess() {  // sum_i w_i in units of 2^-60, minus 2^60 (exact)
+    long long s = 0;
+    for (int i = 0; i < L::Q; i++) s += (long long)(L::wc_[L::cls_[i]] * 1152921504606846976.0);
+    return s - (1ll << 60);
+}
+
+// rho - 1 and j (before the force) from FP64 words; false when a word is
+// outside the exact range (the caller then takes the FP64 formulas).
+template <class L>
+__device__ __forceinline__ bool moments_words(const unsigned long long (&b)[L::Q], ff& dr, ff& jx, ff& jy, ff& jz) {
+    long long sr[3] = {0, 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
+    bool ok = true;
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using K = Link<L, i>;
+        constexpr int cl = K::cls;
+        const long long d = (long long)(b[i] - (unsigned long long)__double_as_longlong(K::w));
+        ok &= within_2p47(d);
+        sr[cl] += d;
+        if constexpr (K::cx > 0) sx[cl] += d;
+        if constexpr (K::cx < 0) sx[cl] -= d;
+        if constexpr (K::cy > 0) sy[cl] += d;
+        if constexpr (K::cy < 0) sy[cl] -= d;
+        if constexpr (K::cz > 0) sz[cl] += d;
+        if constexpr (K::cz < 0) sz[cl] -= d;
+    });
+    constexpr int S0 = FFLink<L, ff_first_of_class<L, 0>()>::SHIFT, S1 = FFLink<L, ff_first_of_class<L, 1>()>::SHIFT,
+                  S2 = FFLink<L, ff_first_of_class<L, 2>()>::SHIFT;
+    const long long r = q60_weight_excess<L>() + (sr[0] << S0) + (sr[1] << S1) + (sr[2] << S2);
+    const long long x = (sx[1] << S1) + (sx[2] << S2), y = (sy[1] << S1) + (sy[2] << S2);
+    const long long z = (sz[1] << S1) + (sz[2] << S2);
+    ok &= small_ll(r, 56) & small_ll(x, 56) & small_ll(y, 56) & small_ll(z, 56);
+    dr = q60_to_ff(r);
+    jx = q60_to_ff(x);
+    jy = q60_to_ff(y);
+    jz = L::D == 3 ? q60_to_ff(z) : ff{0.f, 0.f};
+    return ok;
+}
+
+// The same from FP32 / FP16 words: float-float sums of the deviations (FP32
+// values: of f_i itself, less sum_i w_i = 1 at the end).
+template <class L, class S>
+__device__ __forceinline__ void moments_words(const typename S::T (&raw)[L::Q], const NodeArgs& a, ff& dr, ff& jx,
+                                              ff& jy, ff& jz) {
+    ff r{0.f, 0.f}, x{0.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
+    const float inv_scale = (float)a.f16_inv_scale;  // a power of two
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        using K = Link<L, i>;
+        float g;
+        if constexpr (S::id == LBM_STORE_F16S)
+            g = __half2float(__ushort_as_half(raw[i])) * inv_scale;
+        else
+            g = __uint_as_float(raw[i]);
+        r = ff_acc(r, g);
+        if constexpr (K::cx > 0) x = ff_acc(x, g);
+        if constexpr (K::cx < 0) x = ff_acc(x, -g);
+        if constexpr (K::cy > 0) y = ff_acc(y, g);
+        if constexpr (K::cy < 0) y = ff_acc(y, -g);
+        if constexpr (K::cz > 0) z = ff_acc(z, g);
+        if constexpr (K::cz < 0) z = ff_acc(z, -g);
+    });
+    r = ff_norm(r);
+    if constexpr (S::id == LBM_STORE_F32) r = ff_add(r, ff{-1.f, 0.f});
+    dr = r;
+    jx = ff_norm(x);
+    jy = ff_norm(y);
+    jz = ff_norm(z);
+}
+
 template <class L, int A, int TPB, int MODEL, class S>
-__global__ void __launch_bounds__(TPB* Tile<L, A>::NT) k_moments(const NodeArgs a) {
+__global__ void __launch_bounds__(TPB* Tile<L, A>::NT, TPB* Tile<L, A>::NT > 256 ? 1 : (S::id == LBM_STORE_F64 ? 2 : 3))
+    k_moments(const NodeArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
     constexpr int NTH = TPB * TL::NT;
-    __shared__ NeighShared<TL, TPB> sh;
+    constexpr int PER_TILE = TL::NN * TL::W;
+    static_assert(TPB * PER_TILE <= NTH, "one neighbourhood entry per thread at most");
+    __shared__ NeighShared<TL, TPB> sh[2];
     __shared__ double red[NTH / 32][kStats];
     const int lt = threadIdx.x / TL::NT;
     const int node = threadIdx.x - lt * TL::NT;
-    const int tile = a.tile_begin + blockIdx.x * TPB + lt;
     const int tile_end = a.tile_begin + a.n_tiles;
-    stage_neighbourhood<TL, TPB>(sh, a.nbr, a.tmask, a.tile_off, a.tile_stride, a.tile_begin + blockIdx.x * TPB,
-                                 tile_end, tile, lt, node);
-    __syncthreads();
-    double acc[kStats];
-#pragma unroll
-    for (int k = 0; k < kStats; k++) acc[k] = 0.0;
+    const int n_groups = (a.n_tiles + TPB - 1) / TPB;
     const NodePos<A> p = node_pos<TL>(node);
-    size_t n = 0;
     const bool want_fields = a.rho_out || a.u_out;
-    if (tile < tile_end && mask_bit(sh, lt, TL::CENTER, node) && (!want_fields || dense_index<L, A>(a, tile, p, n))) {
-        T raw[L::Q];
-        gather<L, A, TPB, T>(sh, a.pdf, lt, node, p, raw);
-        double f[L::Q];
-        static_for<0, L::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            f[i] = S::template to_f64<L, i>(raw[i], a.f16_inv_scale);
-        });
-        double rho, jx, jy, jz, ux, uy, uz;
-        moments_f64<L>(f, rho, jx, jy, jz);
-        velocity_f64<L, MODEL>(rho, jx, jy, jz, a.force, ux, uy, uz);
-        const size_t N = (size_t)a.nx * a.ny * a.nz;  // fields only for a single-sample launch
-        if (a.rho_out) a.rho_out[n] = rho;
-        if (a.u_out) {
-            a.u_out[n] = ux;
-            a.u_out[N + n] = uy;
-            if (L::D == 3) a.u_out[2 * N + n] = uz;
+    const size_t N = (size_t)a.nx * a.ny * a.nz;  // fields only for a single-sample launch
+    const ff half_f[3] = {ff_of(0.5 * a.force[0]), ff_of(0.5 * a.force[1]), ff_of(L::D == 3 ? 0.5 * a.force[2] : 0.0)};
+    ff acc_dr{0.f, 0.f}, acc_m[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, acc_u2{0.f, 0.f}, acc_du2{0.f, 0.f};
+    int count = 0;
+
+    // The neighbourhood of the next tile group is staged while this one is
+    // worked on (two buffers): this thread's entry e = (tile, slot, word) is
+    // read as the neighbour index two groups ahead and as the neighbour's
+    // record one group ahead, so no round trip to memory stands between two
+    // groups.
+    const int e = threadIdx.x;
+    const bool has_entry = e < TPB * PER_TILE;
+    const int e_lt = e / PER_TILE, e_rem = e - e_lt * PER_TILE;
+    const int e_slot = e_rem / TL::W, e_w = e_rem - e_slot * TL::W;
+    auto load_nb = [&](int g) {
+        const int t = a.tile_begin + g * TPB + e_lt;
+        return has_entry && t < tile_end ? __ldg(a.nbr + (size_t)t * TL::NN + e_slot) : -1;
+    };
+    auto load_rec = [&](int nb) {
+        if (nb < 0) return make_ulonglong2(0ull, 0ull);
+        if (e_w == 0) return __ldg(a.tinfo + nb);
+        return make_ulonglong2(__ldg(a.tmask + (size_t)nb * TL::W + e_w), 0ull);
+    };
+    auto store = [&](NeighShared<TL, TPB>& s, const ulonglong2 r, long long origin) {
+        if (e == 0) s.origin = origin;
+        if (!has_entry) return;
+        s.m[e_lt][e_slot][e_w] = r.x;
+        if (e_w == 0)
+            s.loc[e_lt][e_slot] = r.y ? make_int2((int)((long long)(r.y >> 24) - origin), (int)(r.y & 0xFFFFFFull))
+                                      : make_int2(0, 0);
+    };
+    const int g0 = blockIdx.x * kMomentGroups;
+    const int g_end = min(n_groups, g0 + kMomentGroups);
+    if (g0 < g_end) store(sh[0], load_rec(load_nb(g0)), __ldg(a.tile_off + a.tile_begin + g0 * TPB));
+    int nb_next = g0 + 1 < g_end ? load_nb(g0 + 1) : -1;
+    __syncthreads();
+    for (int g = g0; g < g_end; g++) {
+        NeighShared<TL, TPB>& cur = sh[(g - g0) & 1];
+        const bool more = g + 1 < g_end;
+        ulonglong2 rec_next = make_ulonglong2(0ull, 0ull);
+        long long origin_next = 0;
+        if (more) {
+            rec_next = load_rec(nb_next);
+            origin_next = __ldg(a.tile_off + a.tile_begin + (g + 1) * TPB);
         }
-        acc[0] = rho;
-        acc[1] = rho * ux;
-        acc[2] = rho * uy;
-        acc[3] = rho * uz;
-        acc[4] = ux * ux + uy * uy + uz * uz;
-        if (a.residual && a.u_saved) {
-            double* us = a.u_saved + (size_t)tile * 3 * TL::NT + node;
-            const double dx = ux - us[0], dy = uy - us[TL::NT], dz = uz - us[2 * TL::NT];
-            acc[5] = dx * dx + dy * dy + dz * dz;
-            us[0] = ux;
-            us[TL::NT] = uy;
-            us[2 * TL::NT] = uz;
+        const int nb_after = g + 2 < g_end ? load_nb(g + 2) : -1;
+        const int tile = a.tile_begin + g * TPB + lt;
+        size_t n = 0;
+        if (tile < tile_end && mask_bit(cur, lt, TL::CENTER, node) && (!want_fields || dense_index<L, A>(a, tile, p, n))) {
+            T raw[L::Q];
+            const int rank = gather<L, A, TPB, T>(cur, a.pdf, lt, node, p, raw);
+            const long long slot = (cur.origin + cur.loc[lt][TL::CENTER].x) / L::Q + rank;
+            float2 prev[3];
+            float2* us = a.residual && a.u_saved ? a.u_saved + slot : nullptr;
+            if (us) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) prev[k] = us[k * a.n_slots];
+            }
+            ff dr, j[3], u[3];
+            bool exact = true;
+            if constexpr (S::id == LBM_STORE_F64)
+                exact = moments_words<L>(raw, dr, j[0], j[1], j[2]);
+            else
+                moments_words<L, S>(raw, a, dr, j[0], j[1], j[2]);
+            if (exact) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) j[k] = ff_add(j[k], half_f[k]);  // j + F/2
+                if constexpr (MODEL == LBM_QUASI_COMPRESSIBLE) {
+                    // 1 / rho as in the float-float step
+                    ff rho = fast2(1.f, dr.h);
+                    rho = fast2(rho.h, __fadd_rn(rho.l, dr.l));
+                    const float r0 = __frcp_rn(rho.h);
+                    const float pr = __fmul_rn(rho.h, r0);
+                    const float pe = __fmaf_rn(rho.h, r0, -pr);
+                    const float er = __fsub_rn(__fsub_rn(__fsub_rn(1.f, pr), pe), __fmul_rn(rho.l, r0));
+                    const ff rinv = fast2(r0, __fmul_rn(r0, er));
+#pragma unroll
+                    for (int k = 0; k < 3; k++) u[k] = ff_norm(ff_mul(j[k], rinv));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) u[k] = j[k];
+                }
+            } else {  // outside the exact range, or not finite: the FP64 formulas
+                double f[L::Q];
+                static_for<0, L::Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = S::template to_f64<L, i>(raw[i], a.f16_inv_scale);
+                });
+                double rho, jx, jy, jz, ux, uy, uz;
+                moments_f64<L>(f, rho, jx, jy, jz);
+                velocity_f64<L, MODEL>(rho, jx, jy, jz, a.force, ux, uy, uz);
+                dr = ff_of(rho - 1.0);
+                j[0] = ff_of(jx + 0.5 * a.force[0]);
+                j[1] = ff_of(jy + 0.5 * a.force[1]);
+                j[2] = ff_of(jz + 0.5 * a.force[2]);
+                u[0] = ff_of(ux);
+                u[1] = ff_of(uy);
+                u[2] = ff_of(uz);
+            }
+            if (a.rho_out) a.rho_out[n] = 1.0 + dbl_of(dr);
+            if (a.u_out) {
+                a.u_out[n] = dbl_of(u[0]);
+                a.u_out[N + n] = dbl_of(u[1]);
+                if (L::D == 3) a.u_out[2 * N + n] = dbl_of(u[2]);
+            }
+            acc_dr = ff_add(acc_dr, dr);
+            // momentum rho u: j + F/2 (Eq. 5); rho (j + F/2) for the incompressible u (Eq. 6)
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                acc_m[k] = ff_add(acc_m[k], MODEL == LBM_QUASI_COMPRESSIBLE ? j[k] : ff_mul(fast2(1.f, dr.h), j[k]));
+            acc_u2 = ff_acc(acc_u2, __fmaf_rn(u[0].h, u[0].h, __fmaf_rn(u[1].h, u[1].h, __fmul_rn(u[2].h, u[2].h))));
+            if (us) {
+                float du2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float d = ff_add(u[k], ff{-prev[k].x, -prev[k].y}).h;
+                    du2 = __fmaf_rn(d, d, du2);
+                    us[k * a.n_slots] = make_float2(u[k].h, u[k].l);
+                }
+                acc_du2 = ff_acc(acc_du2, du2);
+            }
+            count++;
         }
-        acc[6] = 1.0;
+        if (more) store(sh[(g + 1 - g0) & 1], rec_next, origin_next);
+        nb_next = nb_after;
+        __syncthreads();  // the next group's neighbourhood is staged; this one's buffer is free
     }
-    // deterministic block sum: butterfly within each warp, then warps in order
+    // deterministic block sum: float-float butterfly within each warp, then warps in order
+    ff v[6] = {acc_dr, acc_m[0], acc_m[1], acc_m[2], ff_norm(acc_u2), ff_norm(acc_du2)};
 #pragma unroll
-    for (int k = 0; k < kStats; k++)
+    for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+        for (int k = 0; k < 6; k++)
+            v[k] = ff_add(v[k], ff{__shfl_xor_sync(0xffffffffu, v[k].h, off), __shfl_xor_sync(0xffffffffu, v[k].l, off)});
+        count += __shfl_xor_sync(0xffffffffu, count, off);
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
+    if (lane == 0) {
+        red[warp][0] = (double)count + dbl_of(v[0]);  // mass: sum of 1 + (rho - 1)
 #pragma unroll
-        for (int k = 0; k < kStats; k++) red[warp][k] = acc[k];
+        for (int k = 1; k < 6; k++) red[warp][k] = dbl_of(v[k]);
+        red[warp][6] = (double)count;
+        red[warp][7] = 0.0;
+    }
     __syncthreads();
     if (threadIdx.x < kStats) {
         double s = 0.0;
@@ -221,7 +413,8 @@ cudaError_t launch_init(const NodeArgs& a, cudaStream_t s) {
 template <class L, int A, int MODEL, class S>
 cudaError_t launch_moments(const NodeArgs& a, cudaStream_t s) {
     constexpr int TPB = tiles_per_block<L, A>();
-    const int blocks = (a.n_tiles + TPB - 1) / TPB;
+    const int groups = (a.n_tiles + TPB - 1) / TPB;
+    const int blocks = (groups + kMomentGroups - 1) / kMomentGroups;
     if (blocks == 0) return cudaSuccess;
     k_moments<L, A, TPB, MODEL, S><<<blocks, TPB * Tile<L, A>::NT, 0, s>>>(a);
     return cudaGetLastError();
@@ -273,7 +466,8 @@ int node_blocks(int lattice, int a, int n_tiles) {
     const int d = lattice == LBM_D2Q9 ? 2 : 3;
     for (int k = 0; k < d; k++) nt *= a;
     const int tpb = nt >= 256 ? 1 : 256 / nt;
-    return (n_tiles + tpb - 1) / tpb;
+    const int groups = (n_tiles + tpb - 1) / tpb;
+    return (groups + kMomentGroups - 1) / kMomentGroups;
 }
 
 // ---- selection ------------------------------------------------------------------------

@@ -29,7 +29,7 @@ EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_exp
             "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc",
             "lbm_build_tilemap_batch", "lbm_init_batch", "lbm_moments_batch", "lbm_export_pdfs_sample",
             "lbm_num_samples", "lbm_moments_sample", "lbm_filter_period2")
-LBM_NOALLOC_MAX_BLOCKS = 65536
+LBM_NOALLOC_MAX_BLOCKS = 8192
 
 
 class LBMError(RuntimeError):

@@ -63,7 +63,8 @@ def test_noalloc_matches_lbm_moments_twice(lattice, a):
 
 def test_noalloc_rejects_too_many_blocks():
     torch = _cuda()
-    # 257 x 256 tiles of 16^2, one fluid node in each: 65,792 blocks > 65,536
+    # 257 x 256 tiles of 16^2, one fluid node in each: 65,792 tiles in groups
+    # of 8 per partial block = 8,224 blocks > 8,192
     mask = np.zeros((1, 256 * 16, 257 * 16), np.uint8)
     mask[0, 5::16, 7::16] = 1
     s = lbm.Solver(mask, 9, 16, (0, 0, 0), 0.8, (0, 0, 0))
