@@ -288,8 +288,9 @@ def run_ours(args):
     solver.stats(residual=True)
     barrier()
 
-    # the float-float / fixed-point FP64 step is followed by its FP64 fallback kernel
-    kernels_per_step = 2 if (args.storage == "f64" and args.arith != "f64" and args.layout == "t2c") else 1
+    # the D3Q19 float-float / fixed-point FP64 step is followed by its FP64 fallback kernel
+    kernels_per_step = 2 if (args.storage == "f64" and args.arith != "f64" and args.layout == "t2c"
+                             and lat == 19) else 1
     sampler = ClockSampler(local)
     ev = []
     t_start = torch.cuda.Event(enable_timing=True)

@@ -263,9 +263,10 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double) * samples.size()));
     CTRY(cudaMalloc(&c->d_err, sizeof(int)));
     CTRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    // the float-float and fixed-point FP64 steps list out-of-range nodes for a
-    // native-FP64 fallback kernel (at most every fluid node once per step)
-    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith != LBM_ARITH_F64) {
+    // the D3Q19 float-float and fixed-point FP64 steps list out-of-range nodes
+    // for a native-FP64 fallback kernel (at most every fluid node once per
+    // step); D2Q9 recomputes them inside the step
+    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith != LBM_ARITH_F64 && p->lattice == LBM_D3Q19) {
         c->fallback_fn = select_fp64_fallback(p->lattice, p->tile_a, p->model);
         if (!c->fallback_fn) TRY(fail(LBM_ERR_ARG, "no FP64 fallback kernel for this lattice and tile"));
         const size_t cap = T.info.n_fluid > 0 ? (size_t)T.info.n_fluid : 1;

@@ -143,6 +143,23 @@ constexpr int ff_first_of_class() {
     return i;
 }
 
+// The node's update in native FP64 (the range fallback of the float-float and
+// fixed-point steps): the words are gathered again, collided and stored.
+template <class L, int A, int MODEL, int KMAX>
+__device__ __forceinline__ void update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh, const StepArgs& a,
+                                            const WorkNode& wn, const NodePos<A>& p, unsigned long long* out,
+                                            int stride) {
+    unsigned long long b[L::Q];
+    gather<L, A, KMAX, unsigned long long>(sh, a.src, wn.lt, wn.node, p, b);
+    double f[L::Q];
+    static_for<0, L::Q>([&](auto I) { f[decltype(I)::value] = __longlong_as_double((long long)b[decltype(I)::value]); });
+    collide_f64<L, MODEL>(f, a.omega, a.force);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        out[i * stride] = (unsigned long long)__double_as_longlong(f[i]);
+    });
+}
+
 template <class L, int MODEL>
 __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], const FixedConsts& k,
                                            const FFConsts& c, unsigned long long* out, int stride) {

@@ -18,7 +18,6 @@
 // Nodes outside that range (|f_i - w_i| beyond ~w_i/32, |j| >= 1/16,
 // |rho - 1| >= 1/32, NaN, negative values) are recomputed in native FP64.
 #include <cmath>
-#include <cstdlib>
 
 #include "collide_ff.cuh"
 
@@ -37,10 +36,14 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const St
     const int stride = sh.loc[wn.lt][TL::CENTER].y;
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
-        // out of range: listed for the FP64 fallback kernel that follows this one
-        // (the node's list entry is read again rather than kept live)
-        const unsigned k = atomicAdd(a.fb_count, 1u);
-        if (k < a.fb_cap) a.fb_list[k] = __ldg(a.nodes + a.blocks[blockIdx.x].node_begin + threadIdx.x);
+        if constexpr (inline_fp64_fallback<L>()) {
+            update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
+        } else {
+            // out of range: listed for the FP64 fallback kernel that follows this one
+            // (the node's list entry is read again rather than kept live)
+            const unsigned k = atomicAdd(a.fb_count, 1u);
+            if (k < a.fb_cap) a.fb_list[k] = __ldg(a.nodes + a.blocks[blockIdx.x].node_begin + threadIdx.x);
+        }
     }
 }
 
@@ -94,33 +97,21 @@ void ff_consts(const lbm_params* p, FFConsts* k) {
         ff_consts_for<D3Q19>(p, k);
 }
 
-template <class L, int A, int MODEL>
-static StepLaunch pick_minb(int minb) {
-    switch (minb) {
-        case 1: return &launch_step_ff<L, A, MODEL, 1>;
-        case 2: return &launch_step_ff<L, A, MODEL, 2>;
-        default: return &launch_step_ff<L, A, MODEL, 3>;
-    }
-}
-
 template <class L, int A>
-static StepLaunch pick(int model, int minb) {
-    return model == LBM_QUASI_COMPRESSIBLE ? pick_minb<L, A, LBM_QUASI_COMPRESSIBLE>(minb)
-                                           : pick_minb<L, A, LBM_INCOMPRESSIBLE>(minb);
+static StepLaunch pick(int model) {
+    constexpr int MINB = fp64_step_min_blocks<L, A>();
+    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_ff<L, A, LBM_QUASI_COMPRESSIBLE, MINB>
+                                           : &launch_step_ff<L, A, LBM_INCOMPRESSIBLE, MINB>;
 }
 
-// Resident blocks per SM the compiler is asked to allow: LBM_FF_MINBLOCKS.
 StepLaunch select_step_ff(int lattice, int a, int model) {
-    const char* v = std::getenv("LBM_FF_MINBLOCKS");
-    int minb = v ? std::atoi(v) : 3;
-    if (minb < 1 || minb > 3) minb = 3;
     if (lattice == LBM_D2Q9) {
-        if (a == 8) return pick<D2Q9, 8>(model, minb);
-        if (a == 16) return pick<D2Q9, 16>(model, minb);
-        if (a == 32) return pick<D2Q9, 32>(model, minb);
+        if (a == 8) return pick<D2Q9, 8>(model);
+        if (a == 16) return pick<D2Q9, 16>(model);
+        if (a == 32) return pick<D2Q9, 32>(model);
     } else if (lattice == LBM_D3Q19) {
-        if (a == 4) return pick<D3Q19, 4>(model, minb);
-        if (a == 8) return pick<D3Q19, 8>(model, minb);
+        if (a == 4) return pick<D3Q19, 4>(model);
+        if (a == 8) return pick<D3Q19, 8>(model);
     }
     return nullptr;
 }

@@ -26,8 +26,7 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "collide_f64.cuh"
-#include "tile.cuh"
+#include "collide_ff.cuh"
 
 namespace lbm {
 
@@ -183,9 +182,13 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_fixed(const
     const int stride = sh.loc[wn.lt][TL::CENTER].y;
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_fixed<L, MODEL>(b, a.fx, out, stride)) {
-        // out of range: listed for the FP64 fallback kernel that follows this one
-        const unsigned k = atomicAdd(a.fb_count, 1u);
-        if (k < a.fb_cap) a.fb_list[k] = (uint32_t)wn.tile * TL::NT + wn.node;
+        if constexpr (inline_fp64_fallback<L>()) {
+            update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
+        } else {
+            // out of range: listed for the FP64 fallback kernel that follows this one
+            const unsigned k = atomicAdd(a.fb_count, 1u);
+            if (k < a.fb_cap) a.fb_list[k] = (uint32_t)wn.tile * TL::NT + wn.node;
+        }
     }
 }
 
@@ -238,27 +241,11 @@ void fixed_consts(const lbm_params* p, FixedConsts* k) {
         fixed_consts_for<D3Q19>(p, k);
 }
 
-// Resident blocks per SM the compiler is asked to allow (register cap):
-// LBM_FIXED_MINBLOCKS = 1, 2 or 3 (default; measured fastest on GB300).
-static int min_blocks() {
-    const char* v = std::getenv("LBM_FIXED_MINBLOCKS");
-    const int m = v ? std::atoi(v) : 3;
-    return m >= 1 && m <= 3 ? m : 3;
-}
-
-template <class L, int A, int MODEL>
-static StepLaunch pick_minb() {
-    switch (min_blocks()) {
-        case 1: return &launch_step_fixed<L, A, MODEL, 1>;
-        case 2: return &launch_step_fixed<L, A, MODEL, 2>;
-        default: return &launch_step_fixed<L, A, MODEL, 3>;
-    }
-}
-
 template <class L, int A>
 static StepLaunch pick(int model) {
-    return model == LBM_QUASI_COMPRESSIBLE ? pick_minb<L, A, LBM_QUASI_COMPRESSIBLE>()
-                                           : pick_minb<L, A, LBM_INCOMPRESSIBLE>();
+    constexpr int MINB = fp64_step_min_blocks<L, A>();
+    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_fixed<L, A, LBM_QUASI_COMPRESSIBLE, MINB>
+                                           : &launch_step_fixed<L, A, LBM_INCOMPRESSIBLE, MINB>;
 }
 
 StepLaunch select_step_fixed(int lattice, int a, int model) {

@@ -188,6 +188,16 @@ __device__ __forceinline__ T* own_slot(const NeighShared<TL, TPB>& sh, void* pdf
     return static_cast<T*>(pdf) + sh.origin + sh.loc[lt][TL::CENTER].x + rank;
 }
 
+// Where the float-float and fixed-point FP64 steps send a node outside their
+// exact range: D2Q9 recomputes it in native FP64 inside the step (its nine
+// links leave registers to spare); D3Q19 lists it for a follow-up kernel,
+// since the inline FP64 update would hold registers across the whole
+// collision and spill the step.
+template <class L>
+constexpr bool inline_fp64_fallback() {
+    return L::Q == 9;
+}
+
 // ---- storage policies: raw words <-> FP64 values ------------------------------
 struct StoreF64 {
     using T = unsigned long long;
@@ -253,6 +263,14 @@ constexpr int work_tiles() { return 16; }
 struct WorkNode {
     int lt, tile, node;
 };
+
+// Resident blocks per SM the float-float and fixed-point FP64 steps ask the
+// compiler to allow (it caps their registers): three blocks of 256 threads
+// (80 registers; two blocks measured slower), one block of more threads.
+template <class L, int A>
+constexpr int fp64_step_min_blocks() {
+    return work_threads<L, A>() <= 256 ? 3 : 1;
+}
 
 // Stage the neighbourhoods of the block's tiles, then decode this thread's
 // fluid node.  Every thread of the block must call it (it holds the barrier);
