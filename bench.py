@@ -288,9 +288,6 @@ def run_ours(args):
     solver.stats(residual=True)
     barrier()
 
-    # the D3Q19 float-float / fixed-point FP64 step is followed by its FP64 fallback kernel
-    kernels_per_step = 2 if (args.storage == "f64" and args.arith != "f64" and args.layout == "t2c"
-                             and lat == 19) else 1
     sampler = ClockSampler(local)
     ev = []
     t_start = torch.cuda.Event(enable_timing=True)
@@ -306,7 +303,7 @@ def run_ours(args):
         solver.step(k)
         e1.record(stream)
         ev.append((e0, e1, k))
-        launches += k * kernels_per_step
+        launches += k
         left -= k
         if k == STATS_EVERY:
             st = lbm.lbm_stats()

@@ -60,9 +60,6 @@ struct lbm_ctx {
     int gset = 0;             // TGB: ghost set written by the last step (read by the next)
     size_t ghost_set = 0;     // TGB: bytes of one ghost set
     StepLaunch publish_fn = nullptr;
-    StepLaunch fallback_fn = nullptr;  // FP64 update of nodes the float-float / fixed-point step listed
-    unsigned* d_fb = nullptr;          // [count, blocks done]
-    uint32_t* d_fb_list = nullptr;
     std::vector<SampleRange> samples;     // one entry per geometry of a batch
     std::vector<int> part_begin, part_blocks;  // their slices of the partial sums
     StepArgs sa{};
@@ -95,10 +92,6 @@ static int launch_one(lbm_ctx* c, cudaStream_t s) {
     }
     cudaError_t e = c->step_fn(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
-    if (c->fallback_fn) {
-        e = c->fallback_fn(a, s);
-        if (e != cudaSuccess) return cuda_fail(e, "fallback kernel launch");
-    }
     parity(c) = 1 - parity(c);
     return LBM_OK;
 }
@@ -150,8 +143,6 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_result);
     cudaFree(c->d_u_saved);
     cudaFree(c->d_err);
-    cudaFree(c->d_fb);
-    cudaFree(c->d_fb_list);
     cudaFree(c->d_stage);
     delete c;
 }
@@ -263,21 +254,6 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double) * samples.size()));
     CTRY(cudaMalloc(&c->d_err, sizeof(int)));
     CTRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    // the D3Q19 float-float and fixed-point FP64 steps list out-of-range nodes
-    // for a native-FP64 fallback kernel (at most every fluid node once per
-    // step); D2Q9 recomputes them inside the step
-    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith != LBM_ARITH_F64 && p->lattice == LBM_D3Q19) {
-        c->fallback_fn = select_fp64_fallback(p->lattice, p->tile_a, p->model);
-        if (!c->fallback_fn) TRY(fail(LBM_ERR_ARG, "no FP64 fallback kernel for this lattice and tile"));
-        const size_t cap = T.info.n_fluid > 0 ? (size_t)T.info.n_fluid : 1;
-        CTRY(cudaMalloc(&c->d_fb, 2 * sizeof(unsigned)));
-        CTRY(cudaMemsetAsync(c->d_fb, 0, 2 * sizeof(unsigned), s));
-        CTRY(cudaMalloc(&c->d_fb_list, cap * sizeof(uint32_t)));
-        c->sa.fb_count = c->d_fb;
-        c->sa.fb_done = c->d_fb + 1;
-        c->sa.fb_list = c->d_fb_list;
-        c->sa.fb_cap = (unsigned)cap;
-    }
     CTRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
 
     StepArgs& sa = c->sa;

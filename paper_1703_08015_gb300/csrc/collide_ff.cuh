@@ -144,9 +144,11 @@ constexpr int ff_first_of_class() {
 }
 
 // The node's update in native FP64 (the range fallback of the float-float and
-// fixed-point steps): the words are gathered again, collided and stored.
+// fixed-point steps): the words are gathered again, collided and stored.  Not
+// inlined: as a call its registers stay off the step's hot path (inline, the
+// FP64 update held enough registers to spill the whole D3Q19 step).
 template <class L, int A, int MODEL, int KMAX>
-__device__ __forceinline__ void update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh, const StepArgs& a,
+__device__ __noinline__ void update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh, const StepArgs& a,
                                             const WorkNode& wn, const NodePos<A>& p, unsigned long long* out,
                                             int stride) {
     unsigned long long b[L::Q];

@@ -121,10 +121,6 @@ struct StepArgs {
     double f16_inv_scale;
     float omega_f, force_f[3], f16_scale_f, f16_inv_scale_f;
     int* err;             // device error word (0 = none)
-    unsigned* fb_count;   // FP64 fallback: nodes listed by this step (cleared by the fallback kernel)
-    unsigned* fb_done;    // fallback kernel: blocks finished (the last one clears both)
-    uint32_t* fb_list;    // listed nodes, tile * NT + node (capacity fb_cap)
-    unsigned fb_cap;
     FixedConsts fx;
     FFConsts ffc;
     F32Consts f32c;
@@ -164,7 +160,6 @@ using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 StepLaunch select_step(const lbm_params* p);
 void f32_consts(const lbm_params* p, double omega, const double* force, F32Consts* k);
 StepLaunch select_step_tgb(const lbm_params* p);
-StepLaunch select_fp64_fallback(int lattice, int a, int model);
 StepLaunch select_tgb_publish(int lattice, int a, int storage);
 long long tgb_ghost_per_tile(int lattice, int a);
 NodeLaunch select_init(int lattice, int a, int model, int storage);

@@ -36,14 +36,9 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const St
     const int stride = sh.loc[wn.lt][TL::CENTER].y;
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
-        if constexpr (inline_fp64_fallback<L>()) {
-            update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
-        } else {
-            // out of range: listed for the FP64 fallback kernel that follows this one
-            // (the node's list entry is read again rather than kept live)
-            const unsigned k = atomicAdd(a.fb_count, 1u);
-            if (k < a.fb_cap) a.fb_list[k] = __ldg(a.nodes + a.blocks[blockIdx.x].node_begin + threadIdx.x);
-        }
+        // out of range: the same update in native FP64 (a call, so that its
+        // registers do not weigh on the float-float path)
+        update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
     }
 }
 

@@ -182,13 +182,9 @@ __global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_fixed(const
     const int stride = sh.loc[wn.lt][TL::CENTER].y;
     T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
     if (!collide_fixed<L, MODEL>(b, a.fx, out, stride)) {
-        if constexpr (inline_fp64_fallback<L>()) {
-            update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
-        } else {
-            // out of range: listed for the FP64 fallback kernel that follows this one
-            const unsigned k = atomicAdd(a.fb_count, 1u);
-            if (k < a.fb_cap) a.fb_list[k] = (uint32_t)wn.tile * TL::NT + wn.node;
-        }
+        // out of range: the same update in native FP64 (a call, so that its
+        // registers do not weigh on the fixed-point path)
+        update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
     }
 }
 

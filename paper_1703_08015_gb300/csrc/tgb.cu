@@ -127,10 +127,39 @@ __device__ __forceinline__ int gather_tgb(const NeighShared<Tile<L, A>, KMAX>& s
     return own_rank;
 }
 
+// The q FP64 words of a node's update in native FP64, for the nodes outside
+// the range of the float-float arithmetic: a call rather than inline code, so
+// that its registers do not weigh on the step.
+template <int Q>
+struct Words {
+    unsigned long long v[Q];
+};
+
+template <class L, int A, int MODEL, int KMAX>
+__device__ __noinline__ Words<L::Q> tgb_update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh,
+                                                    const int (&nbt)[KMAX][Tile<L, A>::NN], const StepArgs& a,
+                                                    int lt, int node, const NodePos<A>& p) {
+    unsigned long long raw[L::Q];
+    gather_tgb<L, A, KMAX, unsigned long long>(sh, nbt, static_cast<const unsigned long long*>(a.dst),
+                                               static_cast<const unsigned long long*>(a.ghost_in), lt, node, p, raw);
+    double f[L::Q];
+    static_for<0, L::Q>([&](auto I) { f[decltype(I)::value] = __longlong_as_double((long long)raw[decltype(I)::value]); });
+    collide_f64<L, MODEL>(f, a.omega, a.force);
+    Words<L::Q> w;
+    static_for<0, L::Q>([&](auto I) { w.v[decltype(I)::value] = (unsigned long long)__double_as_longlong(f[decltype(I)::value]); });
+    return w;
+}
+
+// Resident blocks per SM requested (register cap) for each arithmetic.
+template <class L, int A, int ARITH>
+constexpr int tgb_min_blocks() {
+    return work_threads<L, A>() > 256 ? 1 : (ARITH == 0 ? 1280 / work_threads<L, A>() : (ARITH == 1 ? 3 : 2));
+}
+
 // ARITH: 0 = FP32 collision on deviations (reduced storage), 1 = float-float
 // FP64 (native FP64 for nodes out of its range), 2 = native FP64.
 template <class L, int A, int MODEL, class S, int ARITH>
-__global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArgs a) {
+__global__ void __launch_bounds__(work_threads<L, A>(), tgb_min_blocks<L, A, ARITH>()) k_step_tgb(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = typename S::T;
     constexpr int E = ghost_per_tile<L, A>();
@@ -138,27 +167,14 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
     __shared__ int nbt[work_tiles()][TL::NN];
     const WorkBlock wb = a.blocks[blockIdx.x];
     T* copy = static_cast<T*>(a.dst);  // the single copy (src == dst)
-    const long long origin = __ldg(a.tile_off + wb.tile_begin);
-    if (threadIdx.x == 0) sh.origin = origin;
-    for (int k = threadIdx.x; k < wb.n_tiles * TL::NN * TL::W; k += blockDim.x) {
-        const int lt = k / (TL::NN * TL::W);
-        const int r = k - lt * (TL::NN * TL::W);
-        const int slot = r / TL::W, w = r - slot * TL::W;
-        const int nb = __ldg(a.nbr + (size_t)(wb.tile_begin + lt) * TL::NN + slot);
-        sh.m[lt][slot][w] = nb >= 0 ? __ldg(a.tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0) {
-            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(a.tile_off + nb) - origin), __ldg(a.tile_stride + nb))
-                                       : make_int2(0, 0);
-            nbt[lt][slot] = nb;
-        }
-    }
-    __syncthreads();
     const bool active = (int)threadIdx.x < wb.count;
+    const uint32_t e = active ? __ldg(a.nodes + wb.node_begin + threadIdx.x) : 0u;  // in flight during the staging
+    stage_tables<TL, work_tiles(), work_threads<L, A>()>(sh, a, wb, nbt);
+    __syncthreads();
     T vals[L::Q];
     int tile = 0, lt = 0, node = 0, rank = 0;
     NodePos<A> p{0, 0, 0};
     if (active) {
-        const uint32_t e = __ldg(a.nodes + wb.node_begin + threadIdx.x);
         tile = (int)(e >> (TL::D * TL::LA));
         node = (int)(e & (TL::NT - 1));
         lt = tile - wb.tile_begin;
@@ -172,9 +188,12 @@ __global__ void __launch_bounds__(work_threads<L, A>()) k_step_tgb(const StepArg
             collide_f32<L, MODEL>(g, a.f32c, a.force_f);
             static_for<0, L::Q>([&](auto I) { vals[decltype(I)::value] = IO::template raw<decltype(I)::value>(g[decltype(I)::value], a); });
         } else {
-            bool done = false;
-            if constexpr (ARITH == 1) done = collide_ff<L, MODEL>(raw, a.fx, a.ffc, vals, 1);
-            if (!done) {
+            if constexpr (ARITH == 1) {
+                if (!collide_ff<L, MODEL>(raw, a.fx, a.ffc, vals, 1)) {
+                    const Words<L::Q> w = tgb_update_fp64<L, A, MODEL, work_tiles()>(sh, nbt, a, lt, node, p);
+                    static_for<0, L::Q>([&](auto I) { vals[decltype(I)::value] = w.v[decltype(I)::value]; });
+                }
+            } else {
                 double f[L::Q];
                 static_for<0, L::Q>([&](auto I) { f[decltype(I)::value] = __longlong_as_double((long long)raw[decltype(I)::value]); });
                 collide_f64<L, MODEL>(f, a.omega, a.force);

@@ -188,16 +188,6 @@ __device__ __forceinline__ T* own_slot(const NeighShared<TL, TPB>& sh, void* pdf
     return static_cast<T*>(pdf) + sh.origin + sh.loc[lt][TL::CENTER].x + rank;
 }
 
-// Where the float-float and fixed-point FP64 steps send a node outside their
-// exact range: D2Q9 recomputes it in native FP64 inside the step (its nine
-// links leave registers to spare); D3Q19 lists it for a follow-up kernel,
-// since the inline FP64 update would hold registers across the whole
-// collision and spill the step.
-template <class L>
-constexpr bool inline_fp64_fallback() {
-    return L::Q == 9;
-}
-
 // ---- storage policies: raw words <-> FP64 values ------------------------------
 struct StoreF64 {
     using T = unsigned long long;
@@ -272,16 +262,15 @@ constexpr int fp64_step_min_blocks() {
     return work_threads<L, A>() <= 256 ? 3 : 1;
 }
 
-// Stage the neighbourhoods of the block's tiles, then decode this thread's
-// fluid node.  Every thread of the block must call it (it holds the barrier);
-// returns false for threads beyond the block's node count.
 // The block's BT threads copy the neighbourhoods of work block `wb`'s tiles
-// into `sh` (visible to the block after the next barrier).  The entries a
-// thread copies are unrolled so that the loads of all of them are in flight
-// together: one round trip for the neighbour indices, one for what they point
-// at, whatever the number of entries per thread.
+// into `sh` (visible to the block after the next barrier), and the neighbour
+// tile indices into `nbt` when given.  The entries a thread copies are
+// unrolled so that the loads of all of them are in flight together: one round
+// trip for the neighbour indices, one for what they point at, whatever the
+// number of entries per thread.
 template <class TL, int KMAX, int BT>
-__device__ __forceinline__ void stage_tables(NeighShared<TL, KMAX>& sh, const StepArgs& a, const WorkBlock& wb) {
+__device__ __forceinline__ void stage_tables(NeighShared<TL, KMAX>& sh, const StepArgs& a, const WorkBlock& wb,
+                                             int (*nbt)[TL::NN] = nullptr) {
     constexpr int PER_TILE = TL::NN * TL::W;
     constexpr int R = (KMAX * PER_TILE + BT - 1) / BT;  // entries per thread, at most
     const long long origin = __ldg(a.tile_off + wb.tile_begin);
@@ -322,11 +311,17 @@ __device__ __forceinline__ void stage_tables(NeighShared<TL, KMAX>& sh, const St
             const int lt = k / PER_TILE, rem = k - lt * PER_TILE;
             const int slot = rem / TL::W, w = rem - slot * TL::W;
             sh.m[lt][slot][w] = m[r];
-            if (w == 0) sh.loc[lt][slot] = loc[r];
+            if (w == 0) {
+                sh.loc[lt][slot] = loc[r];
+                if (nbt) nbt[lt][slot] = nb[r];
+            }
         }
     }
 }
 
+// Stage the neighbourhoods of the block's tiles, then decode this thread's
+// fluid node.  Every thread of the block must call it (it holds the barrier);
+// returns false for threads beyond the block's node count.
 template <class TL, int KMAX, int BT>
 __device__ __forceinline__ bool stage_work_at(NeighShared<TL, KMAX>& sh, const StepArgs& a, int wbi,
                                               WorkNode& wn) {
