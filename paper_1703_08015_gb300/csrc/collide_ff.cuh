@@ -33,6 +33,15 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
     return fast2(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
 }
 
+// x + y without the final renormalisation, for sums that only feed further
+// sums (ff_sum3): the error is the same as ff_add's, but the low part may
+// exceed half an ulp of the high part after cancellation, which a following
+// product would evaluate in single precision.
+__device__ __forceinline__ ff ff_add_lazy(ff x, ff y) {
+    const ff s = two_sum(x.h, y.h);
+    return ff{s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l))};
+}
+
 __device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.h, -x.l}; }
 
 __device__ __forceinline__ ff ff_mul(ff x, ff y) {
@@ -214,10 +223,11 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         RINV = fast2(r0, __fmul_rn(r0, er));
     }
     // gamma = 1.5 w |p|^2 + 3 (1 - w/2) p.F, p = j + F/2
-    const ff jj = ff_add(ff_add(ff_sqr(JX), ff_sqr(JY)), ff_sqr(JZ));
+    // (sums that feed a product are renormalised, the others are lazy)
+    const ff jj = ff_add(ff_add_lazy(ff_sqr(JX), ff_sqr(JY)), ff_sqr(JZ));
     const ff gamma = ff_add(ff_mul(jj, ff_c(c.g1)),
-                            ff_add(ff_add(ff_mul(JX, ff_c(c.kf[0])), ff_mul(JY, ff_c(c.kf[1]))),
-                                   ff_mul(JZ, ff_c(c.kf[2]))));
+                            ff_add_lazy(ff_add_lazy(ff_mul(JX, ff_c(c.kf[0])), ff_mul(JY, ff_c(c.kf[1]))),
+                                        ff_mul(JZ, ff_c(c.kf[2]))));
     // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V,
     // formed at the first link of the class (links come class by class)
     ff V{0.f, 0.f}, C{0.f, 0.f};
@@ -237,10 +247,10 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         using K = Link<L, i>;
         if constexpr (i == ff_first_of_class<L, K::cls>()) {
             V = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[K::cls])) : ff_c(c.w[K::cls]);
-            C = ff_add(ff_mul(DR, ff_c(c.rho[K::cls])), ff_neg(ff_mul(gamma, V)));
+            C = ff_add_lazy(ff_mul(DR, ff_c(c.rho[K::cls])), ff_neg(ff_mul(gamma, V)));
         }
         if constexpr (i == 0) {
-            const ff x = ff_add(kept(I), C);
+            const ff x = ff_add_lazy(kept(I), C);
             store(I, x);
         } else if constexpr (i < K::opp) {
             constexpr int j = K::opp;
@@ -259,8 +269,8 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
             // symmetric part E = C + y (4.5 w y + 9 (1 - w/2) c_i.F) V, antisymmetric part
             // O = 3 w w_c y + 3 (1 - w/2) w_c c_i.F (all in ulps of w_c)
             const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[i])));
-            const ff E = ff_add(C, ff_mul(T, V));
-            const ff O = ff_add(ff_mul(Y, ff_c(c.j[cl])), ff_c(c.so[i]));
+            const ff E = ff_add_lazy(C, ff_mul(T, V));
+            const ff O = ff_add_lazy(ff_mul(Y, ff_c(c.j[cl])), ff_c(c.so[i]));
             store(I, ff_sum3(kept(I), E, O));
             store(std::integral_constant<int, j>{}, ff_sum3(kept(std::integral_constant<int, j>{}), E, ff_neg(O)));
         }
