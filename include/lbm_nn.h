@@ -5,7 +5,8 @@
  * field from a geometry mask so that the lattice Boltzmann solve reaches its
  * steady state in fewer steps; the LBM residual alone still decides
  * convergence.  These entry points are the network's GPU kernels: 3x3x3
- * convolutions on tensor cores (BF16 operands, FP32 accumulation) for the
+ * convolutions on tensor cores (BF16 operands, FP32 accumulation; tcgen05 or
+ * mma.sync by shape) for the
  * forward pass and both backward passes, plus the pooling, upsampling,
  * concatenation, loss and optimiser steps of training.
  *
@@ -37,6 +38,28 @@ extern "C" {
  * same `wrap`. */
 int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
                   const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
+
+/* lbm_nn_conv3d on the 5th-generation tensor cores (tcgen05): an implicit
+ * GEMM of 128 voxels x up to 128 output channels per block, the activations
+ * gathered by cp.async into a three-stage shared-memory ring, the FP32
+ * accumulator in tensor memory.  Same arguments and results; needs cin % 8 ==
+ * 0, cout % 16 == 0 and 16-byte aligned x, wgt, y, y32 (else LBM_ERR_ARG).
+ * lbm_nn_conv3d uses it by itself for 64 or more output channels over 16,384
+ * or more voxels, where it measured faster than the mma.sync kernel. */
+int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
+                     const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
+
+/* c[i][j] = sum_l a[i][l] * b[j][l] on the 5th-generation tensor cores
+ * (tcgen05): a BF16 [m][k], b BF16 [n][k] (both with k contiguous), c FP32
+ * [m][n], row-major, device memory.  Needs m % 128 == 0, n % 16 == 0 with
+ * 16 <= n <= 256, k % 64 == 0 (else LBM_ERR_ARG).  Every wait inside the
+ * kernel is bounded; a block whose wait ran out writes NaN over its rows and
+ * counts itself (lbm_nn_tc_timeouts). */
+int lbm_nn_gemm_bf16(const void* a, const void* b, float* c, int m, int n, int k, void* stream);
+
+/* Number of tensor-core kernel blocks whose bounded waits ran out since the
+ * last call (a device counter, read and cleared; synchronises the device). */
+int lbm_nn_tc_timeouts(unsigned* count);
 
 /* dx-ready weights: wt[tap][co][ci] = wgt[26 - tap][ci][co] (BF16). */
 int lbm_nn_weight_flip(const void* wgt, int cin, int cout, void* wt, void* stream);

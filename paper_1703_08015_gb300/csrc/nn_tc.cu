@@ -1,0 +1,311 @@
+// nn_tc.cu -- GEMMs of the learned warm start on the 5th-generation tensor
+// cores (tcgen05): operands staged in shared memory by the block's threads,
+// the FP32 accumulator in tensor memory (TMEM), one thread issuing the MMAs
+// and an mbarrier reporting their completion.  A plain BF16 GEMM and the
+// 3x3x3 convolution as an implicit GEMM share one pipeline.  See
+// include/lbm_nn.h.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "lbm_nn.h"
+#include "tc.cuh"
+
+namespace lbm {
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+__device__ unsigned g_tc_timeouts;  // blocks of the tensor-core kernels whose waits ran out
+
+constexpr int TC_M = 128;                        // rows per block = accumulator lanes
+constexpr int TC_BK = 64;                        // reduction depth of one stage: four K = 16 MMAs
+constexpr uint32_t TC_KGAP = 128;                // core matrices adjacent along K (leading byte offset)
+constexpr uint32_t TC_RGAP = (TC_BK / 8) * 128;  // 8-row groups (stride byte offset)
+constexpr uint32_t TC_WAIT = 1u << 24;           // polls before a wait gives up
+
+__host__ __device__ constexpr uint32_t tc_stage_bytes(int n) { return (uint32_t)(TC_M + n) * TC_BK * 2; }
+constexpr int TC_STAGES = 3;  // operand stages in flight
+
+// The pipeline of one block: `nk` stages of depth 64 in a ring of TC_STAGES
+// shared-memory buffers.  fill(a, b, kc) stages A (128 x 64) and B (n x 64),
+// K-major, 16-byte row segments at tc::tile_off, with cp.async or plain
+// stores; the copies of the next TC_STAGES - 1 stages are in flight while the
+// tensor cores work on the current one.  Thread 0 issues a stage's four MMAs
+// into the TMEM accumulator and commits them to the stage's mbarrier; a
+// buffer is refilled once the MMAs that read it have completed.  Then every
+// thread reads its accumulator row, 16 columns at a time, into
+// out(row_in_tile, first_column, values, ok).  `n` is a multiple of 16 in
+// 16 .. 256.
+template <class Fill, class Out>
+__device__ __forceinline__ void tc_pipeline(unsigned char* smem, uint64_t* mbar, uint32_t* tmem_slot, int n, int nk,
+                                            Fill fill, Out out) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t a_bytes = TC_M * TC_BK * 2;
+    const uint32_t stage_bytes = tc_stage_bytes(n);
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)n) ncols <<= 1;
+    if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
+    if (tid == 0)
+        for (int s = 0; s < TC_STAGES; s++) tc::mbar_init(&mbar[s], 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, n);
+    bool ok = true;
+    // one cp.async group per stage, empty past the end, so that "all but the
+    // newest TC_STAGES - 2 groups complete" always means "this stage landed"
+    for (int p = 0; p < TC_STAGES - 1; p++) {
+        if (p < nk) fill(smem + p * stage_bytes, smem + p * stage_bytes + a_bytes, p);
+        tc::cp_async_commit();
+    }
+    for (int kc = 0; kc < nk; kc++) {
+        const int s = kc % TC_STAGES;
+        unsigned char* sa = smem + s * stage_bytes;
+        tc::cp_async_wait<TC_STAGES - 2>();
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(sa), b0 = a0 + a_bytes;
+#pragma unroll
+            for (int j = 0; j < TC_BK / 16; j++)
+                tc::mma_bf16(tmem, tc::smem_desc(a0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP),
+                             tc::smem_desc(b0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP), idesc, kc > 0 || j > 0);
+            tc::mma_commit(&mbar[s]);
+        }
+        // refill the buffer of stage kc - 1 with stage kc + TC_STAGES - 1, once its MMAs are done
+        const int nxt = kc + TC_STAGES - 1;
+        if (nxt < nk) {
+            const int r = nxt % TC_STAGES;
+            if (kc >= 1) ok &= tc::mbar_wait(&mbar[r], ((kc - 1) / TC_STAGES) & 1, TC_WAIT);
+            fill(smem + r * stage_bytes, smem + r * stage_bytes + a_bytes, nxt);
+        }
+        tc::cp_async_commit();
+    }
+    // the last commit arrives once every MMA of the block has completed
+    const int last = nk - 1;
+    bool done = tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
+    if (!done) done = tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
+    ok &= done;
+    tc::cp_async_wait<0>();
+    if (!ok && lane == 0) atomicAdd(&g_tc_timeouts, 1u);
+    tc::fence_after_sync();
+    for (int c0 = 0; c0 < n; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        out(warp * 32 + lane, c0, v, ok);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
+// C[m][n] = sum_k A[m][k] B[n][k]: A, B BF16 with K contiguous, C FP32;
+// M % 128 == 0, N % 16 == 0 (16 .. 256), K % 64 == 0.
+__global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, const bf16* __restrict__ B,
+                                                 float* __restrict__ C, int N, int K) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t mbar[TC_STAGES];
+    __shared__ uint32_t tmem_slot;
+    const int m0 = blockIdx.x * TC_M;
+    auto fill = [&](unsigned char* sa, unsigned char* sb, int kc) {
+        for (int e = threadIdx.x; e < TC_M * 8; e += 128) {
+            const int r = e >> 3, g = e & 7;
+            tc::cp_async16(sa + tc::tile_off(r, g, TC_KGAP, TC_RGAP), A + (size_t)(m0 + r) * K + kc * TC_BK + g * 8,
+                           true);
+        }
+        for (int e = threadIdx.x; e < N * 8; e += 128) {
+            const int r = e >> 3, g = e & 7;
+            tc::cp_async16(sb + tc::tile_off(r, g, TC_KGAP, TC_RGAP), B + (size_t)r * K + kc * TC_BK + g * 8, true);
+        }
+    };
+    auto out = [&](int r, int c0, const float (&v)[16], bool ok) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) C[(size_t)(m0 + r) * N + c0 + k] = ok ? v[k] : __int_as_float(0x7fc00000);
+    };
+    tc_pipeline(smem, mbar, &tmem_slot, N, K / TC_BK, fill, out);
+}
+
+// Neighbour coordinate along one axis: zero padding (-1 outside) or periodic.
+__device__ __forceinline__ int tc_nb(int c, int d, int n, bool wrap) {
+    c += d;
+    if (wrap) return c < 0 ? c + n : (c >= n ? c - n : c);
+    return (c < 0 || c >= n) ? -1 : c;
+}
+
+// The 3x3x3 convolution of lbm_nn_conv3d as an implicit GEMM:
+// y[p][co] = act(sum_k A[p][k] B[co][k] + bias[co]) with k = (tap, ci),
+// A[p][(tap, ci)] = x[p + off(tap)][ci] (zero outside, or wrapped on the axes
+// of `wrap`) and B[co][(tap, ci)] = wgt[tap][ci][co].  One block computes 128
+// voxels x NT output channels from blockIdx.y * NT; Cin % 8 == 0 (each 16-byte
+// row segment lies in one tap), NT % 16 == 0.  Rows k >= 27 Cin of the last
+// stage are zero.
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ x, int N, int D, int H, int W, int Cin,
+                                                 const bf16* __restrict__ wgt, const float* __restrict__ bias,
+                                                 int Cout, int NT, int relu, int wrap, bf16* __restrict__ y,
+                                                 float* __restrict__ y32) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t mbar[TC_STAGES];
+    __shared__ uint32_t tmem_slot;
+    const long long M = (long long)N * D * H * W;
+    const int K = 27 * Cin;
+    const long long m0 = (long long)blockIdx.x * TC_M;
+    const int n0 = blockIdx.y * NT;
+    const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
+    // voxel (n, z, y, x) of each of the block's rows (n < 0: past the end)
+    __shared__ int4 vox[TC_M];
+    {
+        const long long p = m0 + threadIdx.x;
+        int4 c = make_int4(-1, 0, 0, 0);
+        if (p < M) {
+            long long t = p;
+            c.w = (int)(t % W);
+            t /= W;
+            c.z = (int)(t % H);
+            t /= H;
+            c.y = (int)(t % D);
+            c.x = (int)(t / D);
+        }
+        vox[threadIdx.x] = c;
+    }
+    __syncthreads();
+    // a thread fills K group g = tid % 8 of rows tid / 8 + 16 j, j = 0 .. 7
+    auto fill = [&](unsigned char* sa, unsigned char* sb, int kc) {
+        const int g = threadIdx.x & 7;
+        const int k = kc * TC_BK + g * 8;
+        const bool kin = k < K;
+        const int tap = kin ? k / Cin : 0, ci = k - tap * Cin;
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int r = (threadIdx.x >> 3) + 16 * j;
+            const int4 c = vox[r];
+            const bf16* src = x;  // a zero fill (padding, past the end) reads nothing
+            bool full = false;
+            if (kin && c.x >= 0) {
+                const int zz = tc_nb(c.y, dz, D, wz), yy = tc_nb(c.z, dy, H, wy), xx = tc_nb(c.w, dx, W, wx);
+                if ((zz | yy | xx) >= 0) {
+                    src = x + ((((long long)c.x * D + zz) * H + yy) * W + xx) * Cin + ci;
+                    full = true;
+                }
+            }
+            tc::cp_async16(sa + tc::tile_off(r, g, TC_KGAP, TC_RGAP), src, full);
+        }
+        // B[co][k] from wgt[k][co]: 8 consecutive co of one k per 16-byte load,
+        // stored down the 8 rows of one segment column
+        for (int e = threadIdx.x; e < TC_BK * (NT / 8); e += 128) {
+            const int kk = e / (NT / 8), c8 = (e - kk * (NT / 8)) * 8;
+            const int k = kc * TC_BK + kk;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k < K && n0 + c8 < Cout) v = *reinterpret_cast<const uint4*>(wgt + (size_t)k * Cout + n0 + c8);
+            const bf16* h = reinterpret_cast<const bf16*>(&v);
+            const int g = kk >> 3, col = kk & 7;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                *reinterpret_cast<bf16*>(sb + tc::tile_off(c8 + j, g, TC_KGAP, TC_RGAP) + col * 2) = h[j];
+        }
+    };
+    // 16 columns of one row (Cout % 16 == 0: a chunk is wholly inside or outside)
+    auto out = [&](int r, int c0, const float (&v)[16], bool ok) {
+        const long long row = m0 + r;
+        const int co0 = n0 + c0;
+        if (row >= M || co0 >= Cout) return;
+        float a[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            a[k] = ok ? v[k] + (bias ? bias[co0 + k] : 0.f) : __int_as_float(0x7fc00000);
+            if (relu) a[k] = fmaxf(a[k], 0.f);
+        }
+        if (y) {
+            uint32_t h[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const __nv_bfloat162 t = __floats2bfloat162_rn(a[2 * k], a[2 * k + 1]);
+                h[k] = *reinterpret_cast<const uint32_t*>(&t);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(y + row * Cout + co0);
+            dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        if (y32) {
+            float4* dst = reinterpret_cast<float4*>(y32 + row * Cout + co0);
+#pragma unroll
+            for (int k = 0; k < 4; k++) dst[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+        }
+    };
+    tc_pipeline(smem, mbar, &tmem_slot, NT, (K + TC_BK - 1) / TC_BK, fill, out);
+}
+
+}  // namespace nn
+}  // namespace lbm
+
+using namespace lbm;
+using namespace lbm::nn;
+
+static int tc_launch_ok(const void* kernel, uint32_t smem, const char* what) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, what);
+}
+
+extern "C" int lbm_nn_gemm_bf16(const void* a, const void* b, float* c, int m, int n, int k, void* stream) {
+    if (!a || !b || !c || m < 1 || n < 16 || n > 256 || k < 1 || m % TC_M || n % 16 || k % TC_BK)
+        return fail(LBM_ERR_ARG, "lbm_nn_gemm_bf16: needs m %% 128 == 0, n %% 16 == 0 in 16..256, k %% 64 == 0");
+    const uint32_t smem = TC_STAGES * tc_stage_bytes(n);
+    int rc = tc_launch_ok((const void*)k_gemm_tc, smem, "cudaFuncSetAttribute(k_gemm_tc)");
+    if (rc) return rc;
+    k_gemm_tc<<<m / TC_M, 128, smem, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(a),
+                                                                           static_cast<const bf16*>(b), c, n, k);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_gemm_tc launch");
+}
+
+namespace lbm {
+namespace nn {
+// The tensor-core convolution for the shapes it takes (cin % 8 == 0, cout %
+// 16 == 0, 16-byte aligned operands); returns 1, launching nothing, for the
+// others.
+int conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
+              int relu, int wrap, void* y, float* y32, cudaStream_t s) {
+    if (cin % 8 || cout % 16 || ((uintptr_t)x | (uintptr_t)wgt | (uintptr_t)y | (uintptr_t)y32) & 15) return 1;
+    const int tiles = (cout + 127) / 128;
+    const int nt = ((cout / tiles + 15) / 16) * 16;
+    const long long M = (long long)n * d * h * w;
+    const long long gx = (M + TC_M - 1) / TC_M;
+    if (gx > 0x7fffffff) return 1;
+    const uint32_t smem = TC_STAGES * tc_stage_bytes(nt);
+    int rc = tc_launch_ok((const void*)k_conv_tc, smem, "cudaFuncSetAttribute(k_conv_tc)");
+    if (rc) return rc;
+    k_conv_tc<<<dim3((unsigned)gx, (unsigned)((cout + nt - 1) / nt)), 128, smem, s>>>(
+        static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt), bias, cout, nt, relu, wrap,
+        static_cast<bf16*>(y), y32);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_conv_tc launch");
+}
+}  // namespace nn
+}  // namespace lbm
+
+extern "C" int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
+                                const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream) {
+    if (!x || !wgt || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (!y && !y32) || (wrap & ~7))
+        return fail(LBM_ERR_ARG, "lbm_nn_conv3d_tc: bad arguments");
+    const int rc = conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, static_cast<cudaStream_t>(stream));
+    if (rc == 1)
+        return fail(LBM_ERR_ARG, "lbm_nn_conv3d_tc: needs cin %% 8 == 0, cout %% 16 == 0 and 16-byte aligned operands");
+    return rc;
+}
+
+extern "C" int lbm_nn_tc_timeouts(unsigned* count) {
+    if (!count) return fail(LBM_ERR_ARG, "lbm_nn_tc_timeouts: NULL argument");
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_tc_timeouts, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_tc_timeouts, &zero, sizeof(unsigned));
+    }
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_nn_tc_timeouts");
+}

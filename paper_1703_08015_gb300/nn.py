@@ -56,6 +56,9 @@ _SIGS = {
     "lbm_nn_target_to_fields": [P, SZ, F64, F64, F64, P, P, P],
     "lbm_nn_f32_to_bf16": [P, SZ, P, P],
     "lbm_nn_bf16_to_f32": [P, SZ, P, P],
+    "lbm_nn_gemm_bf16": [P, P, P, I, I, I, P],
+    "lbm_nn_conv3d_tc": [P, I, I, I, I, I, P, P, I, I, I, P, P, P],
+    "lbm_nn_tc_timeouts": [P],
 }
 EXPORTED = tuple(_SIGS)
 _ready = False
@@ -92,6 +95,23 @@ def _call(name, *args):
 
 
 # ---- the C entry points, same names and argument order (tensors or addresses) ----
+
+def lbm_nn_gemm_bf16(a, b, c, m, n, k, stream=None):
+    _call("lbm_nn_gemm_bf16", _p(a), _p(b), _p(c), m, n, k, stream)
+
+
+def lbm_nn_conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, stream=None):
+    _call("lbm_nn_conv3d_tc", _p(x), n, d, h, w, cin, _p(wgt), _p(bias), cout, int(relu), int(wrap), _p(y),
+          _p(y32), stream)
+
+
+def lbm_nn_tc_timeouts():
+    """Blocks of the tensor-core kernels whose bounded waits ran out since the
+    last call (read and cleared)."""
+    v = ctypes.c_uint(0)
+    _call("lbm_nn_tc_timeouts", ctypes.byref(v))
+    return int(v.value)
+
 
 def lbm_nn_conv3d(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, stream=None):
     _call("lbm_nn_conv3d", _p(x), n, d, h, w, cin, _p(wgt), _p(bias), cout, int(relu), int(wrap), _p(y), _p(y32),

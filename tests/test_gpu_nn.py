@@ -1,5 +1,7 @@
 """GPU tests of the warm-start network kernels against the FP64 reference in
-oracle/nn_ref.py, through the C ABI of include/lbm_nn.h.
+oracle/nn_ref.py, through the C ABI of include/lbm_nn.h.  Convolutions with
+cin % 8 == 0 and cout % 16 == 0 run on the tcgen05 tensor cores, the others on
+the mma.sync kernel; the cases below cover both.
 
 Operands are BF16 values (the reference sees the same values in FP64).  The
 convolutions multiply BF16 pairs exactly and add in FP32, so a result may
@@ -46,21 +48,40 @@ CONV_CASES = [
     (1, 4, 3, 5, 32, 192, 1, 0),
     (1, 2, 4, 4, 7, 9, 0, 5),
     (1, 1, 1, 1, 16, 3, 0, 7),
+    # shapes of the tcgen05 path (cin % 8 == 0, cout % 16 == 0): a partial last
+    # tile of 128 voxels, cin 8 with zero padding, several channel tiles
+    (2, 6, 7, 9, 16, 32, 1, 3),
+    (1, 3, 4, 5, 8, 48, 1, 2),
+    (1, 8, 8, 8, 64, 128, 0, 7),
 ]
 
 
+def _conv(nn, entry):
+    """The convolution entry point under test: lbm_nn_conv3d (which picks the
+    kernel by shape) or lbm_nn_conv3d_tc (tcgen05 tensor cores only)."""
+    return nn.lbm_nn_conv3d if entry == "auto" else nn.lbm_nn_conv3d_tc
+
+
+def _tc_ok(cin, cout):
+    return cin % 8 == 0 and cout % 16 == 0
+
+
+@pytest.mark.parametrize("entry", ["auto", "tc"])
 @pytest.mark.parametrize("case", CONV_CASES)
-def test_conv_forward(nn, case):
+def test_conv_forward(nn, case, entry):
     n, d, h, w, cin, cout, relu, wrap = case
+    if entry == "tc" and not _tc_ok(cin, cout):
+        pytest.skip("shape outside the tcgen05 kernel")
     rng = np.random.default_rng(hash(case) % 2**32)
     x = rand_bf16(rng, (n, d, h, w, cin))
     wt = rand_bf16(rng, (27, cin, cout), 1.0 / np.sqrt(27 * cin))
     b = rng.normal(0, 0.1, cout).astype(np.float32)
     y = torch.empty((n, d, h, w, cout), dtype=torch.bfloat16, device="cuda")
     y32 = torch.empty((n, d, h, w, cout), dtype=torch.float32, device="cuda")
-    nn.lbm_nn_conv3d(bf16_dev(x), n, d, h, w, cin, bf16_dev(wt), torch.from_numpy(b).cuda(), cout, relu, wrap, y,
+    _conv(nn, entry)(bf16_dev(x), n, d, h, w, cin, bf16_dev(wt), torch.from_numpy(b).cuda(), cout, relu, wrap, y,
                      y32)
     torch.cuda.synchronize()
+    assert nn.lbm_nn_tc_timeouts() == 0
     ref = R.conv3d(x, wt, b.astype(np.float64), bool(relu), wrap)
     tol = 2.0 ** -16 * R.conv3d(np.abs(x), np.abs(wt), np.abs(b.astype(np.float64)), False, wrap) + 1e-30
     got = f64(y32)
@@ -69,16 +90,19 @@ def test_conv_forward(nn, case):
     assert np.array_equal(f64(y), R.bf16_round(got))
 
 
-@pytest.mark.parametrize("case", CONV_CASES[:5])
-def test_conv_backward_data_by_flipped_weights(nn, case):
+@pytest.mark.parametrize("entry", ["auto", "tc"])
+@pytest.mark.parametrize("case", CONV_CASES[:5] + CONV_CASES[6:])
+def test_conv_backward_data_by_flipped_weights(nn, case, entry):
     n, d, h, w, cin, cout, _, wrap = case
+    if entry == "tc" and not _tc_ok(cout, cin):
+        pytest.skip("shape outside the tcgen05 kernel")
     rng = np.random.default_rng(7 + hash(case) % 2**31)
     dy = rand_bf16(rng, (n, d, h, w, cout))
     wt = rand_bf16(rng, (27, cin, cout), 1.0 / np.sqrt(27 * cin))
     flipped = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
     nn.lbm_nn_weight_flip(bf16_dev(wt), cin, cout, flipped)
     dx = torch.empty((n, d, h, w, cin), dtype=torch.float32, device="cuda")
-    nn.lbm_nn_conv3d(bf16_dev(dy), n, d, h, w, cout, flipped, None, cin, 0, wrap, None, dx)
+    _conv(nn, entry)(bf16_dev(dy), n, d, h, w, cout, flipped, None, cin, 0, wrap, None, dx)
     torch.cuda.synchronize()
     ref = R.conv3d_bwd_data(dy, wt, wrap)
     tol = 2.0 ** -16 * R.conv3d_bwd_data(np.abs(dy), np.abs(wt), wrap) + 1e-30
@@ -104,16 +128,19 @@ def test_conv_weight_gradient(nn, case):
     assert np.allclose(f64(db) + 0.5, ref_b, rtol=1e-5, atol=1e-4)
 
 
-def test_large_conv_spans_many_tiles(nn):
-    """64 voxels per block: a 2 x 16^3 batch with 16 -> 64 channels runs 128
-    blocks; spot-check outputs against the reference at sampled voxels."""
+@pytest.mark.parametrize("entry", ["auto", "tc"])
+def test_large_conv_spans_many_tiles(nn, entry):
+    """A 4 x 16^3 batch with 16 -> 64 channels (16,384 voxels: the shape class
+    lbm_nn_conv3d sends to the tcgen05 kernel) runs 128 or 256 blocks; every
+    output is checked against the reference."""
     rng = np.random.default_rng(3)
-    n, s, cin, cout = 2, 16, 16, 64
+    n, s, cin, cout = 4, 16, 16, 64
     x = rand_bf16(rng, (n, s, s, s, cin))
     wt = rand_bf16(rng, (27, cin, cout), 0.1)
     y32 = torch.empty((n, s, s, s, cout), dtype=torch.float32, device="cuda")
-    nn.lbm_nn_conv3d(bf16_dev(x), n, s, s, s, cin, bf16_dev(wt), None, cout, 0, 1, None, y32)
+    _conv(nn, entry)(bf16_dev(x), n, s, s, s, cin, bf16_dev(wt), None, cout, 0, 1, None, y32)
     torch.cuda.synchronize()
+    assert nn.lbm_nn_tc_timeouts() == 0
     ref = R.conv3d(x, wt, None, False, 1)
     tol = 2.0 ** -16 * R.conv3d(np.abs(x), np.abs(wt), None, False, 1) + 1e-30
     assert np.all(np.abs(f64(y32) - ref) <= tol)
