@@ -52,7 +52,7 @@ def parse():
                     help="two PDF copies (T2C) or one copy with ghost buffers (TGB)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "steady", "batch"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "steady", "batch", "conv"])
     ap.add_argument("--samples", type=int, default=64)
     ap.add_argument("--max-steps", type=int, default=100000)
     ap.add_argument("--target", type=float, default=1e-6)
@@ -578,6 +578,45 @@ def run_batch(args):
             "clocks": clocks, "gpu_launches": launches}))
 
 
+# the warm-start U-Net's 3x3x3 convolutions at batch 8 (side, cin, cout)
+CONV_LAYERS = [(64, 16, 16), (64, 48, 16), (32, 16, 32), (32, 32, 32), (32, 96, 32), (16, 32, 64), (16, 64, 64),
+               (16, 192, 64), (8, 64, 128), (8, 128, 128)]
+
+
+def run_conv(args):
+    """Time the network's convolutions through lbm_nn_conv3d (kernel picked by
+    shape) and, where the shape allows, lbm_nn_conv3d_tc (tcgen05); one JSON
+    line with TFLOP/s per layer."""
+    import torch
+
+    from paper_1703_08015_gb300 import nn
+
+    batch, reps = 8, max(args.steps // 100, 5)
+    rows = []
+    for side, cin, cout in CONV_LAYERS:
+        x = torch.randn(batch, side, side, side, cin, device="cuda").to(torch.bfloat16)
+        w = (torch.randn(27, cin, cout, device="cuda") * 0.05).to(torch.bfloat16)
+        y = torch.empty(batch, side, side, side, cout, device="cuda", dtype=torch.bfloat16)
+        row = {"layer": f"{batch}x{side}^3 {cin}->{cout}"}
+        for name, f in (("auto", nn.lbm_nn_conv3d), ("tcgen05", nn.lbm_nn_conv3d_tc)):
+            for _ in range(3):
+                f(x, batch, side, side, side, cin, w, None, cout, 1, 1, y, None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f(x, batch, side, side, side, cin, w, None, cout, 1, 1, y, None)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[name + "_us"] = ms * 1e3
+            row[name + "_tflops"] = 2.0 * batch * side ** 3 * 27 * cin * cout / ms / 1e9
+        rows.append(row)
+    print(json.dumps({"metric": "warm-start U-Net 3x3x3 convolution TFLOP/s (BF16, FP32 accumulation)",
+                      "unit": "TFLOP/s", "dtype": "bf16", "data": "synthetic", "layers": rows,
+                      "tc_timeouts": nn.lbm_nn_tc_timeouts()}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -586,6 +625,8 @@ def main():
         run_steady(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "conv":
+        run_conv(args)
     else:
         run_ours(args)
 
