@@ -39,13 +39,14 @@ extern "C" {
 int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
                   const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
 
-/* lbm_nn_conv3d on the 5th-generation tensor cores (tcgen05): an implicit
- * GEMM of 128 voxels x up to 128 output channels per block, the activations
- * gathered by cp.async into a three-stage shared-memory ring, the FP32
- * accumulator in tensor memory.  Same arguments and results; needs cin % 8 ==
- * 0, cout % 16 == 0 and 16-byte aligned x, wgt, y, y32 (else LBM_ERR_ARG).
- * lbm_nn_conv3d uses it by itself for 64 or more output channels over 16,384
- * or more voxels, where it measured faster than the mma.sync kernel. */
+/* lbm_nn_conv3d on the 5th-generation tensor cores (tcgen05), FP32
+ * accumulator in tensor memory.  With cin % 16 == 0 a block computes a brick
+ * of 8 x 16 x 1 voxels and the tensor cores read the activations straight from
+ * a shared-memory halo tile (up to 64 input channels at a time); with cin % 8
+ * == 0 otherwise, an implicit GEMM gathers them into a three-stage ring.  Same
+ * arguments and results; needs cin % 8 == 0, cout % 16 == 0 and 16-byte
+ * aligned x, wgt, y, y32 (else LBM_ERR_ARG).  lbm_nn_conv3d uses the halo-tile
+ * kernel by itself whenever cin % 16 == 0 and cout % 16 == 0. */
 int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
                      const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
 

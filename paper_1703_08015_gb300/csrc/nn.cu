@@ -466,8 +466,8 @@ static int pick_nf(int cout, int* n_tiles) {
 
 namespace lbm {
 namespace nn {
-int conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
-              int relu, int wrap, void* y, float* y32, cudaStream_t s);
+int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
+                int relu, int wrap, void* y, float* y32, cudaStream_t s);
 }  // namespace nn
 }  // namespace lbm
 
@@ -475,13 +475,10 @@ extern "C" int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin,
                              const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream) {
     if (!x || !wgt || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (!y && !y32) || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d: bad arguments");
-    // the tcgen05 kernel where it measured faster (64 or more output channels
-    // over 16,384 or more voxels; its im2col gather limits it below that),
-    // else the mma.sync kernel below
-    if (cout >= 64 && (long long)n * d * h * w >= 16384) {
-        const int tc = conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, S(stream));
-        if (tc != 1) return tc;
-    }
+    // the tcgen05 halo-tile kernel where the shape allows (cin % 16 == 0,
+    // cout % 16 == 0), else the mma.sync kernel below
+    const int tc = conv3d_halo(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, S(stream));
+    if (tc != 1) return tc;
     const long long M = (long long)n * d * h * w;
     int ny = 0;
     const int nf = pick_nf(cout, &ny);

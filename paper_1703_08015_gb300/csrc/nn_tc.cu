@@ -242,6 +242,193 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ x, int
     tc_pipeline(smem, mbar, &tmem_slot, NT, (K + TC_BK - 1) / TC_BK, fill, out);
 }
 
+// The 3x3x3 convolution with the activations read by the tensor cores straight
+// from a shared-memory halo tile (no im2col copy).  A block computes a brick of
+// 8 (x) x 16 (y) x 1 (z) voxels = 128 accumulator rows, x fastest, for NT output
+// channels.  The halo tile holds (8 + 2) x (16 + 2) x 3 voxels of up to 64 input
+// channels as 16-byte cells of 8 channels, laid out [channel group][z][y][x]:
+// for one tap the 8 voxels of a brick line are 8 consecutive cells, i.e. one
+// core matrix, the 16 lines of the brick are 10 cells (160 B) apart and two
+// channel groups one tile plane (540 cells) apart, so an MMA's A operand is a
+// descriptor into the tile at the tap's offset.  B (the weights, K-major per
+// output channel) streams through a three-stage ring as in k_conv_tc.  Input
+// channels beyond 64 are taken in chunks, the tile reloaded once the MMAs of
+// the previous chunk have completed.  Cin % 16 == 0, NT % 16 == 0.
+constexpr int HX = 10, HY = 18, HZ = 3;  // halo tile extent
+constexpr int HCELLS = HX * HY * HZ;     // 540 cells per channel group
+constexpr uint32_t HGAP = HCELLS * 16;   // channel groups (leading byte offset)
+constexpr uint32_t HLINE = HX * 16;      // brick lines (stride byte offset)
+constexpr int HCC = 64;                  // input channels per chunk
+
+// shared memory of a block: the halo tile of min(Cin, 64) channels and the B ring
+__host__ __device__ constexpr uint32_t halo_tile_bytes(int cin) { return (uint32_t)((cin < HCC ? cin : HCC) / 8) * HGAP; }
+__host__ __device__ constexpr uint32_t halo_smem_bytes(int cin, int nt) {
+    return halo_tile_bytes(cin) + TC_STAGES * (uint32_t)nt * TC_BK * 2;
+}
+
+// Halo-tile coordinate c (the box's coordinate, possibly -1 .. n) along an
+// axis of n voxels: periodic or zero padding; -1 (a zero cell) as well beyond
+// one voxel past either edge, where only rows outside the box would read it.
+__device__ __forceinline__ int halo_nb(int c, int n, bool wrap) {
+    if (c < -1 || c > n) return -1;
+    if (wrap) return c < 0 ? c + n : (c >= n ? c - n : c);
+    return (c < 0 || c >= n) ? -1 : c;
+}
+
+__global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, int N, int D, int H, int W, int Cin,
+                                                   const bf16* __restrict__ wgt, const float* __restrict__ bias,
+                                                   int Cout, int NT, int relu, int wrap, bf16* __restrict__ y,
+                                                   float* __restrict__ y32) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t mbar[TC_STAGES];
+    __shared__ uint32_t tmem_slot;
+    unsigned char* const tile = smem;
+    unsigned char* const ring = smem + halo_tile_bytes(Cin);
+    const uint32_t bstage = (uint32_t)NT * TC_BK * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int BX = (W + 7) / 8, BY = (H + 15) / 16;
+    int b = blockIdx.x;
+    const int xb = b % BX;
+    b /= BX;
+    const int yb = b % BY;
+    b /= BY;
+    const int z0 = b % D, n0 = b / D;
+    const int x0 = xb * 8, y0 = yb * 16;
+    const int c0 = blockIdx.y * NT;
+    const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
+
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)NT) ncols <<= 1;
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, ncols);
+    if (tid == 0)
+        for (int s = 0; s < TC_STAGES; s++) tc::mbar_init(&mbar[s], 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, NT);
+    const uint32_t tile_a = tc::smem_u32(tile);
+    bool ok = true;
+    int g = 0;  // stages issued by the block so far (selects the ring buffer and mbarrier phase)
+
+    // B[co][k] of chunk k = tap * cc + ci (ci < cc) from wgt[tap][cb + ci][c0 + co]
+    auto fill_b = [&](unsigned char* sb, int cb, int cc, int kc) {
+        const int kk_n = 27 * cc;
+        for (int e = tid; e < TC_BK * (NT / 8); e += 128) {
+            const int kk = e / (NT / 8), c8 = (e - kk * (NT / 8)) * 8;
+            const int k = kc * TC_BK + kk;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k < kk_n && c0 + c8 < Cout) {
+                const int tap = k / cc, ci = k - tap * cc;
+                v = *reinterpret_cast<const uint4*>(wgt + ((size_t)tap * Cin + cb + ci) * Cout + c0 + c8);
+            }
+            const bf16* h = reinterpret_cast<const bf16*>(&v);
+            const int gk = kk >> 3, col = kk & 7;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                *reinterpret_cast<bf16*>(sb + tc::tile_off(c8 + j, gk, TC_KGAP, TC_RGAP) + col * 2) = h[j];
+        }
+    };
+
+    for (int cb = 0; cb < Cin; cb += HCC) {
+        const int cc = Cin - cb < HCC ? Cin - cb : HCC;
+        const int nk = (27 * cc + TC_BK - 1) / TC_BK;
+        if (cb > 0) {  // every MMA that reads the tile has completed
+            const int last = g - 1;
+            ok &= tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
+        }
+        // the halo tile of this chunk (zero outside the box, wrapped on periodic axes)
+        for (int e = tid; e < (cc / 8) * HCELLS; e += 128) {
+            const int cg = e / HCELLS, cell = e - cg * HCELLS;
+            const int hx = cell % HX, hy = (cell / HX) % HY, hz = cell / (HX * HY);
+            const int zz = halo_nb(z0 + hz - 1, D, wz), yy = halo_nb(y0 + hy - 1, H, wy),
+                      xx = halo_nb(x0 + hx - 1, W, wx);
+            const bool full = (zz | yy | xx) >= 0;
+            const bf16* src = full ? x + ((((long long)n0 * D + zz) * H + yy) * W + xx) * Cin + cb + cg * 8 : x;
+            tc::cp_async16(tile + (size_t)e * 16, src, full);
+        }
+        // the ring's first stages join the tile's copies in the first group
+        for (int p = 0; p < TC_STAGES - 1; p++) {
+            if (p < nk) fill_b(ring + ((g + p) % TC_STAGES) * bstage, cb, cc, p);
+            tc::cp_async_commit();
+        }
+        for (int kc = 0; kc < nk; kc++, g++) {
+            const int s = g % TC_STAGES;
+            tc::cp_async_wait<TC_STAGES - 2>();
+            tc::fence_smem_to_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t b0 = tc::smem_u32(ring + s * bstage);
+#pragma unroll
+                for (int j = 0; j < TC_BK / 16; j++) {
+                    const int k = kc * TC_BK + 16 * j;
+                    if (k >= 27 * cc) break;
+                    const int tap = k / cc, ci = k - tap * cc;
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // 0 .. 2: offsets -1 .. +1
+                    const uint32_t a = tile_a + (uint32_t)(ci / 8) * HGAP + (uint32_t)((dz * HY + dy) * HX + dx) * 16;
+                    tc::mma_bf16(tmem, tc::smem_desc(a, HGAP, HLINE),
+                                 tc::smem_desc(b0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP), idesc, cb > 0 || kc > 0 || j > 0);
+                }
+                tc::mma_commit(&mbar[s]);
+            }
+            const int nxt = kc + TC_STAGES - 1;
+            if (nxt < nk) {
+                const int r = (g + TC_STAGES - 1) % TC_STAGES;
+                if (kc >= 1) ok &= tc::mbar_wait(&mbar[r], ((g - 1) / TC_STAGES) & 1, TC_WAIT);
+                fill_b(ring + r * bstage, cb, cc, nxt);
+            }
+            tc::cp_async_commit();
+        }
+        tc::cp_async_wait<0>();
+    }
+    const int last = g - 1;
+    bool done = tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
+    if (!done) done = tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
+    ok &= done;
+    if (!ok && lane == 0) atomicAdd(&g_tc_timeouts, 1u);
+    tc::fence_after_sync();
+    // row r of the accumulator = voxel (x0 + r % 8, y0 + r / 8, z0) of sample n0
+    const int r = warp * 32 + lane;
+    const int vx = x0 + (r & 7), vy = y0 + (r >> 3);
+    const bool inside = vx < W && vy < H;
+    const long long row = (((long long)n0 * D + z0) * H + vy) * W + vx;
+    for (int cq = 0; cq < NT; cq += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cq, v);
+        const int co0 = c0 + cq;
+        if (!inside || co0 >= Cout) continue;
+        float a[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            a[k] = ok ? v[k] + (bias ? bias[co0 + k] : 0.f) : __int_as_float(0x7fc00000);
+            if (relu) a[k] = fmaxf(a[k], 0.f);
+        }
+        if (y) {
+            uint32_t h[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const __nv_bfloat162 t = __floats2bfloat162_rn(a[2 * k], a[2 * k + 1]);
+                h[k] = *reinterpret_cast<const uint32_t*>(&t);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(y + row * Cout + co0);
+            dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        if (y32) {
+            float4* dst = reinterpret_cast<float4*>(y32 + row * Cout + co0);
+#pragma unroll
+            for (int k = 0; k < 4; k++) dst[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
 }  // namespace nn
 }  // namespace lbm
 
@@ -290,11 +477,36 @@ int conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wg
 }  // namespace nn
 }  // namespace lbm
 
+namespace lbm {
+namespace nn {
+// The halo-tile tensor-core convolution (cin % 16 == 0, cout % 16 == 0,
+// 16-byte aligned operands); returns 1, launching nothing, for other shapes.
+int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
+                int relu, int wrap, void* y, float* y32, cudaStream_t s) {
+    if (cin % 16 || cout % 16 || ((uintptr_t)x | (uintptr_t)wgt | (uintptr_t)y | (uintptr_t)y32) & 15) return 1;
+    const int tiles = (cout + 127) / 128;
+    const int nt = ((cout / tiles + 15) / 16) * 16;
+    const long long blocks = (long long)n * d * ((h + 15) / 16) * ((w + 7) / 8);
+    if (blocks > 0x7fffffff) return 1;
+    const uint32_t smem = halo_smem_bytes(cin, nt);
+    int rc = tc_launch_ok((const void*)k_conv_halo, smem, "cudaFuncSetAttribute(k_conv_halo)");
+    if (rc) return rc;
+    k_conv_halo<<<dim3((unsigned)blocks, (unsigned)((cout + nt - 1) / nt)), 128, smem, s>>>(
+        static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt), bias, cout, nt, relu, wrap,
+        static_cast<bf16*>(y), y32);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_conv_halo launch");
+}
+}  // namespace nn
+}  // namespace lbm
+
 extern "C" int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wgt,
                                 const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream) {
     if (!x || !wgt || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (!y && !y32) || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_tc: bad arguments");
-    const int rc = conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, static_cast<cudaStream_t>(stream));
+    // the halo-tile kernel for cin % 16 == 0, else the im2col one (cin % 8 == 0)
+    int rc = conv3d_halo(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, static_cast<cudaStream_t>(stream));
+    if (rc == 1) rc = conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, static_cast<cudaStream_t>(stream));
     if (rc == 1)
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_tc: needs cin %% 8 == 0, cout %% 16 == 0 and 16-byte aligned operands");
     return rc;

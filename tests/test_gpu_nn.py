@@ -1,7 +1,8 @@
 """GPU tests of the warm-start network kernels against the FP64 reference in
 oracle/nn_ref.py, through the C ABI of include/lbm_nn.h.  Convolutions with
-cin % 8 == 0 and cout % 16 == 0 run on the tcgen05 tensor cores, the others on
-the mma.sync kernel; the cases below cover both.
+cin % 16 == 0 and cout % 16 == 0 run on the tcgen05 tensor cores (a halo tile
+in shared memory), the others on the mma.sync kernel; the cases below cover
+both, and the tcgen05 im2col kernel (cin % 8 == 0) through lbm_nn_conv3d_tc.
 
 Operands are BF16 values (the reference sees the same values in FP64).  The
 convolutions multiply BF16 pairs exactly and add in FP32, so a result may
@@ -58,7 +59,8 @@ CONV_CASES = [
 
 def _conv(nn, entry):
     """The convolution entry point under test: lbm_nn_conv3d (which picks the
-    kernel by shape) or lbm_nn_conv3d_tc (tcgen05 tensor cores only)."""
+    kernel by shape) or lbm_nn_conv3d_tc (tcgen05 tensor cores only: the
+    halo-tile kernel for cin % 16 == 0, the im2col one for cin % 8 == 0)."""
     return nn.lbm_nn_conv3d if entry == "auto" else nn.lbm_nn_conv3d_tc
 
 
@@ -130,8 +132,7 @@ def test_conv_weight_gradient(nn, case):
 
 @pytest.mark.parametrize("entry", ["auto", "tc"])
 def test_large_conv_spans_many_tiles(nn, entry):
-    """A 4 x 16^3 batch with 16 -> 64 channels (16,384 voxels: the shape class
-    lbm_nn_conv3d sends to the tcgen05 kernel) runs 128 or 256 blocks; every
+    """A 4 x 16^3 batch with 16 -> 64 channels (128 halo-tile blocks); every
     output is checked against the reference."""
     rng = np.random.default_rng(3)
     n, s, cin, cout = 4, 16, 16, 64
