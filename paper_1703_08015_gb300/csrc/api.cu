@@ -40,6 +40,7 @@ struct lbm_ctx {
     int cur = 0;  // copy holding the current post-collision state
     int64_t step = 0;
     int32_t* d_nbr = nullptr;
+    int32_t* d_gtab = nullptr;  // gather table of the FP64 float-float step
     uint64_t* d_tmask = nullptr;
     int32_t* d_coords = nullptr;
     uint32_t* d_nodes = nullptr;
@@ -132,6 +133,7 @@ static void release(lbm_ctx* c) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     if (c->cap) cudaStreamDestroy(c->cap);
     cudaFree(c->d_nbr);
+    cudaFree(c->d_gtab);
     cudaFree(c->d_tmask);
     cudaFree(c->d_coords);
     cudaFree(c->d_nodes);
@@ -266,6 +268,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.tile_stride = c->d_tile_stride;
     sa.tinfo = c->d_tinfo;
     sa.n_tiles = nf;
+    sa.n_nodes = (long long)T.nodes.size();
     sa.tau = p->tau;
     sa.omega = 1.0 / p->tau;
     for (int k = 0; k < 3; k++) sa.force[k] = (k < 2 || p->lattice == LBM_D3Q19) ? p->force[k] : 0.0;
@@ -279,6 +282,22 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.err = c->d_err;
     fixed_consts(&c->p, &sa.fx);
     ff_consts(&c->p, &sa.ffc);
+    // the FP64 float-float step reads its sources from a gather table built
+    // once here (4 (q + 1) bytes per fluid node), when value indices fit int32
+    if (!c->tgb && p->storage == LBM_STORE_F64 && (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO) &&
+        !p->persistent && (!p->block_nodes || p->block_nodes == work_threads_for(p->lattice, p->tile_a)) &&
+        T.info.pdf_bytes / 8 < (size_t)INT32_MAX && sa.n_nodes > 0) {
+        StepLaunch table_step = select_step_ff_table(p->lattice, p->tile_a, p->model);
+        StepLaunch build = select_gather_table_builder(p->lattice, p->tile_a);
+        if (table_step && build) {
+            CTRY(cudaMalloc(&c->d_gtab, (size_t)(c->q + 1) * (size_t)sa.n_nodes * sizeof(int32_t)));
+            sa.gtab = c->d_gtab;
+            sa.gtab_out = c->d_gtab;
+            sa.gtab_pitch = sa.n_nodes;
+            CTRY(build(sa, s));
+            c->step_fn = table_step;
+        }
+    }
 
     NodeArgs& na = c->na;  // a launch over every tile; sample launches narrow it
     na.nbr = c->d_nbr;

@@ -114,6 +114,10 @@ struct StepArgs {
     const int32_t* tile_stride; // compact layout: values per link of each tile
     const ulonglong2* tinfo;    // per tile, one 16-byte record: {first fluid-mask word, tile_off << 24 | tile_stride}
     int n_tiles;
+    long long n_nodes;          // fluid nodes (entries of the work list)
+    const int32_t* gtab;        // FP64 gather table [q + 1][gtab_pitch] (see k_gather_table) or NULL
+    int32_t* gtab_out;          // the same table, written once at initialisation
+    long long gtab_pitch;
     double omega;         // 1 / tau
     double tau;
     double force[3];
@@ -160,6 +164,10 @@ using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 StepLaunch select_step(const lbm_params* p);
 void f32_consts(const lbm_params* p, double omega, const double* force, F32Consts* k);
 StepLaunch select_step_tgb(const lbm_params* p);
+// The float-float FP64 step that reads its sources from a gather table, and
+// the kernel that builds the table once (nullptr when not compiled).
+StepLaunch select_step_ff_table(int lattice, int a, int model);
+StepLaunch select_gather_table_builder(int lattice, int a);
 StepLaunch select_tgb_publish(int lattice, int a, int storage);
 long long tgb_ghost_per_tile(int lattice, int a);
 NodeLaunch select_init(int lattice, int a, int model, int storage);
