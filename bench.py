@@ -315,8 +315,9 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     step_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
     ms_max, value = replica_throughput(ms, n_fluid, args.steps, world, dev)
+    # "ff": float-float through the gather table (the default); "ff_staged": --arith ff
     arith_name = {lbm.LBM_ARITH_AUTO: "ff", lbm.LBM_ARITH_FIXED: "fixed", lbm.LBM_ARITH_F64: "f64",
-                  lbm.LBM_ARITH_FF: "ff"}[arith]
+                  lbm.LBM_ARITH_FF: "ff_staged"}[arith]
     tiling = solver.tiling
     solver.close()
     del solver

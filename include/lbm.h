@@ -75,7 +75,7 @@ extern "C" {
 /* Arithmetic of the FP64 step.  All variants compute the same FP64 update;
  * they differ only in rounding (see lbm_step).  Nodes outside the range of
  * the fixed-point and float-float forms fall back to native FP64. */
-#define LBM_ARITH_AUTO   0 /* = LBM_ARITH_FF */
+#define LBM_ARITH_AUTO   0 /* LBM_ARITH_FF, the sources read from a gather table (below) */
 #define LBM_ARITH_F64    1 /* native FP64 instructions */
 #define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions */
 #define LBM_ARITH_FF     3 /* exact integer sums, float-float products (~48 bits), no FP64 instructions */
@@ -188,7 +188,12 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
  * Asynchronous on `stream`.  With LBM_ARITH_FIXED the FP64 update is computed
  * with 64-bit fixed-point integers (resolution 2^-60), with LBM_ARITH_FF
  * with exact integer sums and float-float products; either is rounded once to
- * FP64 and agrees with LBM_ARITH_F64 to rounding.
+ * FP64 and agrees with LBM_ARITH_F64 to rounding.  LBM_ARITH_AUTO is the
+ * float-float update with the gather resolved once: lbm_init builds a table
+ * of every node's source slots (4 (q + 1) bytes per fluid node, allocated by
+ * the library, T2C layout, when the copy's value indices fit int32; else the
+ * staged gather of LBM_ARITH_FF), and the step reads it instead of staging
+ * the neighbourhood.
  * Errors: LBM_ERR_ARG (NULL ctx, nsteps < 0), LBM_ERR_CUDA. */
 int lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 

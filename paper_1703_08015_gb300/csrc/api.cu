@@ -282,9 +282,10 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.err = c->d_err;
     fixed_consts(&c->p, &sa.fx);
     ff_consts(&c->p, &sa.ffc);
-    // the FP64 float-float step reads its sources from a gather table built
-    // once here (4 (q + 1) bytes per fluid node), when value indices fit int32
-    if (!c->tgb && p->storage == LBM_STORE_F64 && (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO) &&
+    // LBM_ARITH_AUTO: the FP64 float-float step reads its sources from a
+    // gather table built once here (4 (q + 1) bytes per fluid node), when value
+    // indices fit int32; LBM_ARITH_FF keeps the staged step (no table)
+    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith == LBM_ARITH_AUTO &&
         !p->persistent && (!p->block_nodes || p->block_nodes == work_threads_for(p->lattice, p->tile_a)) &&
         T.info.pdf_bytes / 8 < (size_t)INT32_MAX && sa.n_nodes > 0) {
         StepLaunch table_step = select_step_ff_table(p->lattice, p->tile_a, p->model);
