@@ -1,14 +1,15 @@
 // tile.cuh -- device side of the tiled step: staging of a tile's
 // neighbourhood in shared memory and the gather (streaming) of Fig. 5.
 //
-// One thread owns one node of one tile (row order, Sec. 3.2); TPB tiles share
-// a thread block.  Before the single barrier, the threads of a tile copy the
-// tile's 3^d neighbour record into shared memory as base pointers of the
-// neighbours' PDF blocks, together with the neighbours' fluid-node bit masks
-// (the copy of the tile bitmap and the node types of the tile and its halo
-// that Fig. 5 stages).  After the barrier every fluid node pulls f*_i(r - c_i) from the
-// tile that holds r - c_i, or, when that node is solid, in a removed tile or
-// beyond a wall, its own f*_{opp(i)}(r) (halfway bounce-back).
+// One thread owns one fluid node; a block takes the fluid nodes of up to 16
+// consecutive tiles (a work block).  Before the single barrier, the block's
+// threads copy the 3^d neighbour record of each of its tiles into shared
+// memory as offsets of the neighbours' PDF blocks, together with the
+// neighbours' fluid-node bit masks (the copy of the tile bitmap and the node
+// types of the tile and its halo that Fig. 5 stages).  After the barrier every
+// fluid node pulls f*_i(r - c_i) from the tile that holds r - c_i, or, when
+// that node is solid, in a removed tile or beyond a wall, its own
+// f*_{opp(i)}(r) (halfway bounce-back).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -40,25 +41,6 @@ __device__ __forceinline__ int fluid_rank(const uint64_t* m, int n) {
             if (k < w) r += __popcll(m[k]);
     }
     return r;
-}
-
-// Threads of one tile cooperatively stage the neighbourhood of `tile`.
-template <class TL, int TPB>
-__device__ __forceinline__ void stage_neighbourhood(NeighShared<TL, TPB>& sh, const int32_t* __restrict__ nbr,
-                                                    const uint64_t* __restrict__ tmask,
-                                                    const long long* __restrict__ tile_off,
-                                                    const int32_t* __restrict__ tile_stride,
-                                                    int first_tile, int n_tiles, int tile, int lt, int node) {
-    const long long origin = __ldg(tile_off + first_tile);
-    if (lt == 0 && node == 0) sh.origin = origin;
-    for (int k = node; k < TL::NN * TL::W; k += TL::NT) {
-        const int slot = k / TL::W, w = k - slot * TL::W;
-        const int nb = tile < n_tiles ? __ldg(nbr + (size_t)tile * TL::NN + slot) : -1;
-        sh.m[lt][slot][w] = nb >= 0 ? __ldg(tmask + (size_t)nb * TL::W + w) : 0ull;
-        if (w == 0)
-            sh.loc[lt][slot] = nb >= 0 ? make_int2((int)(__ldg(tile_off + nb) - origin), __ldg(tile_stride + nb))
-                                       : make_int2(0, 0);
-    }
 }
 
 // Fluid bit of node n and, when set, its rank (see fluid_rank): the word is
