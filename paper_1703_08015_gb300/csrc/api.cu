@@ -290,13 +290,16 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         T.info.pdf_bytes / 8 < (size_t)INT32_MAX && sa.n_nodes > 0) {
         StepLaunch table_step = select_step_ff_table(p->lattice, p->tile_a, p->model);
         StepLaunch build = select_gather_table_builder(p->lattice, p->tile_a);
-        if (table_step && build) {
-            CTRY(cudaMalloc(&c->d_gtab, (size_t)(c->q + 1) * (size_t)sa.n_nodes * sizeof(int32_t)));
+        const size_t bytes = (size_t)(c->q + 1) * (size_t)sa.n_nodes * sizeof(int32_t);
+        cudaError_t ae = table_step && build ? cudaMalloc(&c->d_gtab, bytes) : cudaErrorInvalidValue;
+        if (ae == cudaSuccess) {
             sa.gtab = c->d_gtab;
             sa.gtab_out = c->d_gtab;
             sa.gtab_pitch = sa.n_nodes;
             CTRY(build(sa, s));
             c->step_fn = table_step;
+        } else if (ae == cudaErrorMemoryAllocation) {
+            (void)cudaGetLastError();  // no room for the table: the staged step needs none
         }
     }
 
