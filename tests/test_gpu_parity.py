@@ -43,7 +43,9 @@ def run_both(oracle, mask, lattice, a, per, tau, F, steps, model=0, arith=lbm.LB
     return gpu, ref
 
 
-ARITHS = [lbm.LBM_ARITH_F64, lbm.LBM_ARITH_FIXED, lbm.LBM_ARITH_FF]
+# native FP64, fixed point, float-float with the staged gather, float-float
+# through the gather table (LBM_ARITH_AUTO, the default)
+ARITHS = [lbm.LBM_ARITH_F64, lbm.LBM_ARITH_FIXED, lbm.LBM_ARITH_FF, lbm.LBM_ARITH_AUTO]
 
 
 def _small_cases():
@@ -62,7 +64,7 @@ def _small_cases():
     ]
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff", "auto"])
 @pytest.mark.parametrize("case", _small_cases(), ids=lambda c: c[0])
 def test_parity_small(oracle, case, arith):
     name, mask, lattice, a, per, tau, F, steps, model = case
@@ -71,7 +73,7 @@ def test_parity_small(oracle, case, arith):
     assert err <= TOL, (name, err)
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff", "auto"])
 def test_parity_d2q9_circles_128_full(oracle, arith):
     """128^2 circles, 16^2 tiles, tau 0.8, F = 1e-6, 1000 steps, every node."""
     mask, params, _ = geo.workload("d2q9_circles_128")
@@ -80,7 +82,7 @@ def test_parity_d2q9_circles_128_full(oracle, arith):
     assert max_rel(gpu, ref, mask) <= TOL
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff", "auto"])
 def test_parity_d3q19_spheres_64_2000_steps(oracle, arith):
     """A 64^3 piece of the sphere-pack workload at its full step count."""
     mask, _ = geo.sphere_pack_3d(64, seed=21)
@@ -119,7 +121,7 @@ def test_full_size_sampled_step_and_mass(oracle, name):
     assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-13
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff", "auto"])
 def test_moments_and_stats(oracle, arith):
     _cuda()
     mask, _ = geo.sphere_pack_3d(shape=(20, 17, 15), seed=5, r_min=2, r_max=4, target_fluid=0.5)
@@ -166,7 +168,7 @@ def test_checkpoint_resume_is_bit_exact():
     assert st.step == 150
 
 
-@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff"])
+@pytest.mark.parametrize("arith", ARITHS, ids=["f64", "fixed", "ff", "auto"])
 def test_edge_cases(oracle, arith):
     _cuda()
     # all solid: nothing to do, nothing to sum
@@ -324,13 +326,14 @@ def test_filter_period2_shortens_the_run_to_steady_state():
     assert err(u_filt) < 0.1 * err(u_plain)
 
 
-@pytest.mark.parametrize("arith", [lbm.LBM_ARITH_FF, lbm.LBM_ARITH_FIXED], ids=["ff", "fixed"])
+@pytest.mark.parametrize("arith", [lbm.LBM_ARITH_FF, lbm.LBM_ARITH_FIXED, lbm.LBM_ARITH_AUTO],
+                         ids=["ff", "fixed", "auto"])
 def test_fp64_fallback_far_from_equilibrium(oracle, arith):
     """A start far from equilibrium (velocity ramping from 0 to 0.02 along y)
     sends most nodes out of the float-float / fixed-point range (|f_i - w_i|
-    beyond about w_i / 32, |u| > ~0.006); they are listed and updated by the
-    native-FP64 fallback kernel, the rest by the fast path, and the whole
-    state still meets the 1e-12 bar."""
+    beyond about w_i / 32, |u| > ~0.006); they take the native-FP64 call
+    inside the step (staged or through the gather table), the rest the fast
+    path, and the whole state still meets the 1e-12 bar."""
     _cuda()
     mask, _ = geo.sphere_pack_3d(shape=(24, 22, 18), seed=12, r_min=2, r_max=4, target_fluid=0.55)
     nz, ny, nx = mask.shape
