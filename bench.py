@@ -243,11 +243,15 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     nf = int(crop.sum())
     v = nf * args.steps / dt / 1e6
-    line = {"impl": "reference", "metric": "D3Q19 sparse MLUPS" if lat == 19 else "D2Q9 sparse MLUPS",
+    # the same metric, unit and workload as our arm; each step a bounded sample of it
+    line = {"impl": "reference",
+            "metric": "D3Q19 sparse MLUPS + % HBM roofline" if lat == 19 else "D2Q9 sparse MLUPS + % HBM roofline",
             "value": v, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "crop": list(crop.shape[::-1]), "fluid_nodes": nf},
+            "config": {"workload": args.workload, "lattice": f"D{3 if lat == 19 else 2}Q{lat}",
+                       "size": list(mask.shape[::-1]), "tile": params["tile_a"], "storage": "f64",
+                       "sample_crop": list(crop.shape[::-1]), "sample_fluid_nodes": nf},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(0), "kind": "oracle",
                              "sample": f"each step: one oracle step on the 64^3 corner crop ({nf} fluid nodes)"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
