@@ -204,20 +204,27 @@ def cpu_baseline(mask, params, seconds=10.0, min_steps=2):
     crop = np.ascontiguousarray(mask[:64, :64, :64]) if mask.shape[0] > 1 else np.ascontiguousarray(mask)
     lat = params["lattice"]
     per = params["periodic"]
-    f = oracle.init(lat, crop)
-    g = np.empty_like(f)
-    oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)  # warm-up
-    n = 0
-    t0 = time.perf_counter()
-    while n < min_steps or time.perf_counter() - t0 < seconds:
-        oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g)
-        f, g = g, f
-        n += 1
-    dt = time.perf_counter() - t0
     nf = int(crop.sum())
+
+    def timed(nthreads, secs):
+        f = oracle.init(lat, crop)
+        g = np.empty_like(f)
+        oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g, nthreads=nthreads)  # warm-up
+        n = 0
+        t0 = time.perf_counter()
+        while n < min_steps or time.perf_counter() - t0 < secs:
+            oracle.step(lat, crop, per, params["tau"], params["force"], f, out=g, nthreads=nthreads)
+            f, g = g, f
+            n += 1
+        return n, time.perf_counter() - t0
+
+    n, dt = timed(0, seconds)
+    n1, dt1 = timed(1, seconds / 3)
     return {"value": nf * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(0), "kind": "oracle",
+            "value_1_thread": nf * n1 / dt1 / 1e6,
             "sample": f"{n} oracle steps on the {crop.shape[2]}x{crop.shape[1]}x{crop.shape[0]} corner "
-                      f"crop ({nf} fluid nodes) of the workload, {dt:.1f} s"}
+                      f"crop ({nf} fluid nodes) of the workload, {dt:.1f} s on all threads; "
+                      f"{n1} steps, {dt1:.1f} s on one thread (value_1_thread)"}
 
 
 def run_reference(args):
