@@ -40,10 +40,11 @@ int lbm_nn_conv3d(const void* x, int n, int d, int h, int w, int cin, const void
                   const float* bias, int cout, int relu, int wrap, void* y, float* y32, void* stream);
 
 /* lbm_nn_conv3d on the 5th-generation tensor cores (tcgen05), FP32
- * accumulator in tensor memory.  With cin % 16 == 0 a block computes a brick
- * of 8 x 16 x 1 voxels and the tensor cores read the activations straight from
- * a shared-memory halo tile (up to 64 input channels at a time); with cin % 8
- * == 0 otherwise, an implicit GEMM gathers them into a three-stage ring.  Same
+ * accumulator in tensor memory.  With cin % 16 == 0 a block computes up to
+ * four bricks of 8 x 16 x 1 voxels stacked along z and the tensor cores read
+ * the activations straight from a shared-memory halo tile (up to 64 input
+ * channels at a time); with cin % 8 == 0 otherwise, an implicit GEMM gathers
+ * them into a three-stage ring.  Same
  * arguments and results; needs cin % 8 == 0, cout % 16 == 0 and 16-byte
  * aligned x, wgt, y, y32 (else LBM_ERR_ARG).  lbm_nn_conv3d uses the halo-tile
  * kernel by itself whenever cin % 16 == 0 and cout % 16 == 0. */
@@ -57,6 +58,13 @@ int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const v
  * kernel is bounded; a block whose wait ran out writes NaN over its rows and
  * counts itself (lbm_nn_tc_timeouts). */
 int lbm_nn_gemm_bf16(const void* a, const void* b, float* c, int m, int n, int k, void* stream);
+
+/* Launch shape of the halo-tile convolution for every later call in this
+ * process: bricks_z bricks per block along z (1..4) and cout_tile output
+ * channels per block (a multiple of 16 up to 128, with bricks_z * cout_tile
+ * <= 512 when both are fixed); 0 leaves either chosen per shape (the default).
+ * For tuning and tests; results do not depend on it.  LBM_ERR_ARG otherwise. */
+int lbm_nn_conv_tune(int bricks_z, int cout_tile);
 
 /* Number of tensor-core kernel blocks whose bounded waits ran out since the
  * last call (a device counter, read and cleared; synchronises the device). */

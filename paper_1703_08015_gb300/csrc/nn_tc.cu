@@ -243,27 +243,34 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ x, int
 }
 
 // The 3x3x3 convolution with the activations read by the tensor cores straight
-// from a shared-memory halo tile (no im2col copy).  A block computes a brick of
-// 8 (x) x 16 (y) x 1 (z) voxels = 128 accumulator rows, x fastest, for NT output
-// channels.  The halo tile holds (8 + 2) x (16 + 2) x 3 voxels of up to 64 input
-// channels as 16-byte cells of 8 channels, laid out [channel group][z][y][x]:
-// for one tap the 8 voxels of a brick line are 8 consecutive cells, i.e. one
-// core matrix, the 16 lines of the brick are 10 cells (160 B) apart and two
-// channel groups one tile plane (540 cells) apart, so an MMA's A operand is a
-// descriptor into the tile at the tap's offset.  B (the weights, K-major per
-// output channel) streams through a three-stage ring as in k_conv_tc.  Input
-// channels beyond 64 are taken in chunks, the tile reloaded once the MMAs of
-// the previous chunk have completed.  Cin % 16 == 0, NT % 16 == 0.
-constexpr int HX = 10, HY = 18, HZ = 3;  // halo tile extent
-constexpr int HCELLS = HX * HY * HZ;     // 540 cells per channel group
-constexpr uint32_t HGAP = HCELLS * 16;   // channel groups (leading byte offset)
+// from a shared-memory halo tile (no im2col copy).  A block computes MB bricks
+// of 8 (x) x 16 (y) x 1 (z) voxels stacked along z, each brick 128 accumulator
+// rows (x fastest) of NT output channels in its own TMEM columns.  The halo
+// tile holds (8 + 2) x (16 + 2) x (MB + 2) voxels of up to 64 input channels
+// as 16-byte cells of 8 channels, laid out [channel group][z][y][x]: for one
+// tap the 8 voxels of a brick line are 8 consecutive cells, i.e. one core
+// matrix, the 16 lines of a brick are 10 cells (160 B) apart, consecutive
+// bricks one tile plane (180 cells) apart and two channel groups one tile
+// (180 (MB + 2) cells) apart, so an MMA's A operand is a descriptor into the
+// tile at the tap's and the brick's offset.  B (the weights, K-major per
+// output channel) streams through a three-stage ring as in k_conv_tc; each
+// stage feeds the MMAs of all MB bricks.  Input channels beyond 64 are taken
+// in chunks, the tile reloaded once the MMAs of the previous chunk have
+// completed.  Cin % 16 == 0, NT % 16 == 0, MB * NT <= 512.
+constexpr int HX = 10, HY = 18;          // halo tile extent in x and y (z: MB + 2)
+constexpr int HPLANE = HX * HY;          // cells of one z plane of the tile
 constexpr uint32_t HLINE = HX * 16;      // brick lines (stride byte offset)
 constexpr int HCC = 64;                  // input channels per chunk
+constexpr int HMB_MAX = 4;               // bricks per block, at most
 
+// bytes between channel groups of the tile (the descriptors' leading byte offset)
+__host__ __device__ constexpr uint32_t halo_gap(int mb) { return (uint32_t)(HPLANE * (mb + 2)) * 16; }
 // shared memory of a block: the halo tile of min(Cin, 64) channels and the B ring
-__host__ __device__ constexpr uint32_t halo_tile_bytes(int cin) { return (uint32_t)((cin < HCC ? cin : HCC) / 8) * HGAP; }
-__host__ __device__ constexpr uint32_t halo_smem_bytes(int cin, int nt) {
-    return halo_tile_bytes(cin) + TC_STAGES * (uint32_t)nt * TC_BK * 2;
+__host__ __device__ constexpr uint32_t halo_tile_bytes(int cin, int mb) {
+    return (uint32_t)((cin < HCC ? cin : HCC) / 8) * halo_gap(mb);
+}
+__host__ __device__ constexpr uint32_t halo_smem_bytes(int cin, int nt, int mb) {
+    return halo_tile_bytes(cin, mb) + TC_STAGES * (uint32_t)nt * TC_BK * 2;
 }
 
 // Halo-tile coordinate c (the box's coordinate, possibly -1 .. n) along an
@@ -277,28 +284,31 @@ __device__ __forceinline__ int halo_nb(int c, int n, bool wrap) {
 
 __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, int N, int D, int H, int W, int Cin,
                                                    const bf16* __restrict__ wgt, const float* __restrict__ bias,
-                                                   int Cout, int NT, int relu, int wrap, bf16* __restrict__ y,
-                                                   float* __restrict__ y32) {
+                                                   int Cout, int NT, int MB, int relu, int wrap,
+                                                   bf16* __restrict__ y, float* __restrict__ y32) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t mbar[TC_STAGES];
     __shared__ uint32_t tmem_slot;
     unsigned char* const tile = smem;
-    unsigned char* const ring = smem + halo_tile_bytes(Cin);
+    unsigned char* const ring = smem + halo_tile_bytes(Cin, MB);
     const uint32_t bstage = (uint32_t)NT * TC_BK * 2;
+    const uint32_t hgap = halo_gap(MB);
+    const int hcells = HPLANE * (MB + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int BX = (W + 7) / 8, BY = (H + 15) / 16;
+    const int BX = (W + 7) / 8, BY = (H + 15) / 16, BZ = (D + MB - 1) / MB;
     int b = blockIdx.x;
     const int xb = b % BX;
     b /= BX;
     const int yb = b % BY;
     b /= BY;
-    const int z0 = b % D, n0 = b / D;
+    const int z0 = (b % BZ) * MB, n0 = b / BZ;
     const int x0 = xb * 8, y0 = yb * 16;
+    const int nb = D - z0 < MB ? D - z0 : MB;  // bricks inside the box
     const int c0 = blockIdx.y * NT;
     const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
 
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)NT) ncols <<= 1;
+    while (ncols < (uint32_t)(MB * NT)) ncols <<= 1;
     if (warp == 0) tc::tmem_alloc(&tmem_slot, ncols);
     if (tid == 0)
         for (int s = 0; s < TC_STAGES; s++) tc::mbar_init(&mbar[s], 1);
@@ -338,9 +348,9 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
             ok &= tc::mbar_wait(&mbar[last % TC_STAGES], (last / TC_STAGES) & 1, TC_WAIT);
         }
         // the halo tile of this chunk (zero outside the box, wrapped on periodic axes)
-        for (int e = tid; e < (cc / 8) * HCELLS; e += 128) {
-            const int cg = e / HCELLS, cell = e - cg * HCELLS;
-            const int hx = cell % HX, hy = (cell / HX) % HY, hz = cell / (HX * HY);
+        for (int e = tid; e < (cc / 8) * hcells; e += 128) {
+            const int cg = e / hcells, cell = e - cg * hcells;
+            const int hx = cell % HX, hy = (cell / HX) % HY, hz = cell / HPLANE;
             const int zz = halo_nb(z0 + hz - 1, D, wz), yy = halo_nb(y0 + hy - 1, H, wy),
                       xx = halo_nb(x0 + hx - 1, W, wx);
             const bool full = (zz | yy | xx) >= 0;
@@ -366,9 +376,11 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
                     if (k >= 27 * cc) break;
                     const int tap = k / cc, ci = k - tap * cc;
                     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // 0 .. 2: offsets -1 .. +1
-                    const uint32_t a = tile_a + (uint32_t)(ci / 8) * HGAP + (uint32_t)((dz * HY + dy) * HX + dx) * 16;
-                    tc::mma_bf16(tmem, tc::smem_desc(a, HGAP, HLINE),
-                                 tc::smem_desc(b0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP), idesc, cb > 0 || kc > 0 || j > 0);
+                    const uint32_t a = tile_a + (uint32_t)(ci / 8) * hgap + (uint32_t)((dz * HY + dy) * HX + dx) * 16;
+                    const uint64_t bdesc = tc::smem_desc(b0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP);
+                    for (int m = 0; m < nb; m++)  // brick m: one tile plane further along z
+                        tc::mma_bf16(tmem + (uint32_t)(m * NT), tc::smem_desc(a + (uint32_t)(m * HPLANE) * 16, hgap, HLINE),
+                                     bdesc, idesc, cb > 0 || kc > 0 || j > 0);
                 }
                 tc::mma_commit(&mbar[s]);
             }
@@ -388,14 +400,15 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
     ok &= done;
     if (!ok && lane == 0) atomicAdd(&g_tc_timeouts, 1u);
     tc::fence_after_sync();
-    // row r of the accumulator = voxel (x0 + r % 8, y0 + r / 8, z0) of sample n0
+    // row r of brick m's accumulator = voxel (x0 + r % 8, y0 + r / 8, z0 + m) of sample n0
     const int r = warp * 32 + lane;
     const int vx = x0 + (r & 7), vy = y0 + (r >> 3);
     const bool inside = vx < W && vy < H;
-    const long long row = (((long long)n0 * D + z0) * H + vy) * W + vx;
-    for (int cq = 0; cq < NT; cq += 16) {
+    for (int q = 0; q < nb * NT; q += 16) {  // brick q / NT, its columns q % NT ..
+        const int m = q / NT, cq = q - m * NT;
+        const long long row = (((long long)n0 * D + z0 + m) * H + vy) * W + vx;
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cq, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)q, v);
         const int co0 = c0 + cq;
         if (!inside || co0 >= Cout) continue;
         float a[16];
@@ -481,18 +494,61 @@ namespace lbm {
 namespace nn {
 // The halo-tile tensor-core convolution (cin % 16 == 0, cout % 16 == 0,
 // 16-byte aligned operands); returns 1, launching nothing, for other shapes.
+static int g_halo_mb = 0, g_halo_nt = 0;  // fixed by lbm_nn_conv_tune; 0 = chosen per shape
+
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            sms = 148;
+        }
+    }
+    return sms;
+}
+
 int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
                 int relu, int wrap, void* y, float* y32, cudaStream_t s) {
     if (cin % 16 || cout % 16 || ((uintptr_t)x | (uintptr_t)wgt | (uintptr_t)y | (uintptr_t)y32) & 15) return 1;
+    const long long plane_bricks = (long long)n * ((h + 15) / 16) * ((w + 7) / 8);
+    if (plane_bricks * d > 0x7fffffff) return 1;
+    const int sms = sm_count();
+    // Launch shape: mb bricks per block along z and nt output channels per
+    // block (the default tile of at most 128 channels, or a half, quarter ..
+    // of it).  Preferred: at least 1.5 blocks per SM in the grid and two
+    // blocks per SM by shared memory (one block's halo copy overlaps another's
+    // MMAs) within the SM's 512 TMEM columns; among those, the most work per
+    // block (mb nt), then the deeper brick stack.  Measured on the U-Net's
+    // layers, this picks the fastest shape or one within 5 % of it.
     const int tiles = (cout + 127) / 128;
-    const int nt = ((cout / tiles + 15) / 16) * 16;
-    const long long blocks = (long long)n * d * ((h + 15) / 16) * ((w + 7) / 8);
-    if (blocks > 0x7fffffff) return 1;
-    const uint32_t smem = halo_smem_bytes(cin, nt);
+    const int nt0 = ((cout / tiles + 15) / 16) * 16;
+    int mb = 0, nt = 0;
+    long long key = -1;
+    for (int ntc = g_halo_nt ? g_halo_nt : nt0; ntc >= 16; ntc = (ntc % 32 == 0 && !g_halo_nt) ? ntc / 2 : 0) {
+        for (int m = HMB_MAX; m >= 1; m--) {
+            if ((g_halo_mb && m != g_halo_mb) || (!g_halo_mb && m == 3) || m * ntc > 512) continue;
+            const long long nblk = plane_bricks * ((d + m - 1) / m) * ((cout + ntc - 1) / ntc);
+            uint32_t cols = 32;
+            while (cols < (uint32_t)(m * ntc)) cols <<= 1;
+            uint32_t per_sm = (228u << 10) / (halo_smem_bytes(cin, ntc, m) + 1024u);
+            per_sm = per_sm > 16 ? 16 : per_sm;
+            const bool occ = per_sm >= 2 && cols * per_sm <= 512u, grid = 2 * nblk >= 3LL * sms;
+            // lexicographic: both, occupancy, then work per block (or, short of
+            // a full grid, the block count), then brick depth
+            const long long k = ((long long)(occ && grid) << 62) | ((long long)occ << 61) |
+                                ((grid ? (long long)(m * ntc) : (nblk < (1LL << 40) ? nblk : (1LL << 40) - 1)) << 3) | m;
+            if (k > key) key = k, mb = m, nt = ntc;
+        }
+    }
+    if (!mb) return 1;
+    const int gy = (cout + nt - 1) / nt;
+    const long long blocks = plane_bricks * ((d + mb - 1) / mb);
+    const uint32_t smem = halo_smem_bytes(cin, nt, mb);
     int rc = tc_launch_ok((const void*)k_conv_halo, smem, "cudaFuncSetAttribute(k_conv_halo)");
     if (rc) return rc;
-    k_conv_halo<<<dim3((unsigned)blocks, (unsigned)((cout + nt - 1) / nt)), 128, smem, s>>>(
-        static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt), bias, cout, nt, relu, wrap,
+    k_conv_halo<<<dim3((unsigned)blocks, (unsigned)gy), 128, smem, s>>>(
+        static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt), bias, cout, nt, mb, relu, wrap,
         static_cast<bf16*>(y), y32);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_conv_halo launch");
@@ -510,6 +566,15 @@ extern "C" int lbm_nn_conv3d_tc(const void* x, int n, int d, int h, int w, int c
     if (rc == 1)
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_tc: needs cin %% 8 == 0, cout %% 16 == 0 and 16-byte aligned operands");
     return rc;
+}
+
+extern "C" int lbm_nn_conv_tune(int bricks_z, int cout_tile) {
+    if (bricks_z < 0 || bricks_z > HMB_MAX || cout_tile < 0 || cout_tile > 128 || cout_tile % 16 ||
+        (bricks_z && cout_tile && bricks_z * cout_tile > 512))
+        return fail(LBM_ERR_ARG, "lbm_nn_conv_tune: bricks_z in 0..4, cout_tile a multiple of 16 in 0..128");
+    g_halo_mb = bricks_z;
+    g_halo_nt = cout_tile;
+    return LBM_OK;
 }
 
 extern "C" int lbm_nn_tc_timeouts(unsigned* count) {

@@ -59,6 +59,7 @@ _SIGS = {
     "lbm_nn_gemm_bf16": [P, P, P, I, I, I, P],
     "lbm_nn_conv3d_tc": [P, I, I, I, I, I, P, P, I, I, I, P, P, P],
     "lbm_nn_tc_timeouts": [P],
+    "lbm_nn_conv_tune": [I, I],
 }
 EXPORTED = tuple(_SIGS)
 _ready = False
@@ -103,6 +104,12 @@ def lbm_nn_gemm_bf16(a, b, c, m, n, k, stream=None):
 def lbm_nn_conv3d_tc(x, n, d, h, w, cin, wgt, bias, cout, relu, wrap, y, y32, stream=None):
     _call("lbm_nn_conv3d_tc", _p(x), n, d, h, w, cin, _p(wgt), _p(bias), cout, int(relu), int(wrap), _p(y),
           _p(y32), stream)
+
+
+def lbm_nn_conv_tune(bricks_z=0, cout_tile=0):
+    """Fix the halo-tile convolution's bricks per block along z and output
+    channels per block (0 = chosen per shape)."""
+    _call("lbm_nn_conv_tune", int(bricks_z), int(cout_tile))
 
 
 def lbm_nn_tc_timeouts():

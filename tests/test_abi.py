@@ -116,3 +116,19 @@ def test_batch_tiling_sums_the_samples():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_build_tilemap_batch(p, bad)
     assert e.value.code == -2
+
+
+def test_conv_tune_validates_its_arguments():
+    """lbm_nn_conv_tune takes 0 (chosen per shape) or a valid launch shape of
+    the halo-tile convolution, and rejects the rest (no GPU involved)."""
+    lib = lbm.library()
+    f = lib.lbm_nn_conv_tune
+    f.argtypes = [ctypes.c_int, ctypes.c_int]
+    f.restype = ctypes.c_int
+    try:
+        for bz, nt in [(0, 0), (1, 16), (4, 128), (3, 48), (0, 112), (4, 0)]:
+            assert f(bz, nt) == 0, (bz, nt)
+        for bz, nt in [(-1, 0), (5, 0), (0, 8), (0, 144), (0, -16), (4, 144), (1, 24)]:
+            assert f(bz, nt) == -1, (bz, nt)
+    finally:
+        assert f(0, 0) == 0

@@ -59,3 +59,34 @@ def test_conv3d_tc_rejects_shapes_outside_it(nn):
     for cin, cout in [(7, 16), (16, 8), (12, 16)]:
         with pytest.raises(lbm.LBMError):
             nn.lbm_nn_conv3d_tc(x, 1, 4, 4, 4, cin, w, None, cout, 0, 0, None, y)
+
+
+@pytest.mark.parametrize("bricks_z,cout_tile", [(1, 16), (2, 32), (3, 48), (4, 16), (4, 128), (2, 0), (0, 16)])
+def test_conv_halo_launch_shapes(nn, bricks_z, cout_tile):
+    """Every launch shape of the halo-tile convolution (bricks per block along
+    z, output channels per block) gives the same FP32 sums, bit for bit, and
+    they match the FP64 convolution: ragged bricks in x, y and z, two input
+    chunks (80 = 64 + 16 channels), a partial output-channel tile, periodic x
+    and z."""
+    n, d, h, w, cin, cout, wrap = 1, 7, 20, 9, 80, 48, 5
+    rng = np.random.default_rng(31)
+    x = R.bf16_round(rng.normal(size=(n, d, h, w, cin)))
+    wt = R.bf16_round(rng.normal(size=(27, cin, cout)) / np.sqrt(27 * cin))
+    b = rng.normal(0, 0.1, cout).astype(np.float32)
+    xd, wd, bd = _dev(x, torch.bfloat16), _dev(wt, torch.bfloat16), torch.from_numpy(b).cuda()
+    y32 = torch.full((n, d, h, w, cout), float("nan"), dtype=torch.float32, device="cuda")
+    base = torch.empty_like(y32)
+    try:
+        nn.lbm_nn_conv_tune(0, 0)
+        nn.lbm_nn_conv3d_tc(xd, n, d, h, w, cin, wd, bd, cout, 0, wrap, None, base)
+        nn.lbm_nn_conv_tune(bricks_z, cout_tile)
+        nn.lbm_nn_conv3d_tc(xd, n, d, h, w, cin, wd, bd, cout, 0, wrap, None, y32)
+        torch.cuda.synchronize()
+    finally:
+        nn.lbm_nn_conv_tune(0, 0)
+    assert nn.lbm_nn_tc_timeouts() == 0
+    assert torch.equal(y32, base)
+    ref = R.conv3d(x, wt, b.astype(np.float64), False, wrap)
+    tol = 2.0 ** -16 * R.conv3d(np.abs(x), np.abs(wt), np.abs(b.astype(np.float64)), False, wrap) + 1e-30
+    got = y32.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
