@@ -51,7 +51,6 @@ struct lbm_ctx {
     double* d_partials = nullptr;
     double* d_result = nullptr;
     float2* d_u_saved = nullptr;
-    int* d_err = nullptr;
     double* d_stage = nullptr;  // dense staging for host outputs
     size_t stage_bytes = 0;
     int nblocks = 0;            // blocks of the node kernels (= partial sums)
@@ -144,7 +143,6 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_u_saved);
-    cudaFree(c->d_err);
     cudaFree(c->d_stage);
     delete c;
 }
@@ -254,8 +252,6 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     }
     CTRY(cudaMalloc(&c->d_partials, (size_t)n_partials * 8 * sizeof(double)));
     CTRY(cudaMalloc(&c->d_result, 8 * sizeof(double) * samples.size()));
-    CTRY(cudaMalloc(&c->d_err, sizeof(int)));
-    CTRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     CTRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
 
     StepArgs& sa = c->sa;
@@ -279,7 +275,6 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     f32_consts(&c->p, sa.omega, sa.force, &sa.f32c);
     sa.f16_scale_f = (float)sa.f16_scale;
     sa.f16_inv_scale_f = (float)sa.f16_inv_scale;
-    sa.err = c->d_err;
     fixed_consts(&c->p, &sa.fx);
     ff_consts(&c->p, &sa.ffc);
     // LBM_ARITH_AUTO: the FP64 float-float step reads its sources from a

@@ -124,7 +124,6 @@ struct StepArgs {
     double f16_scale;     // storage scale for LBM_STORE_F16S
     double f16_inv_scale;
     float omega_f, force_f[3], f16_scale_f, f16_inv_scale_f;
-    int* err;             // device error word (0 = none)
     FixedConsts fx;
     FFConsts ffc;
     F32Consts f32c;
