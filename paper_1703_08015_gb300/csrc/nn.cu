@@ -468,6 +468,8 @@ namespace lbm {
 namespace nn {
 int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
                 int relu, int wrap, void* y, float* y32, cudaStream_t s);
+int wgrad_tc(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout, int wrap, float* dw,
+             cudaStream_t s);
 }  // namespace nn
 }  // namespace lbm
 
@@ -517,6 +519,16 @@ extern "C" int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, 
                                    int wrap, float* dw, float* dbias, void* stream) {
     if (!x || !dy || !dw || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_wgrad: bad arguments");
+    // the tcgen05 GEMMs over packed operands where the shape allows, else the
+    // gather kernel below
+    int rc = wgrad_tc(x, dy, n, d, h, w, cin, cout, wrap, dw, S(stream));
+    if (rc != 1) {
+        if (rc || !dbias) return rc;
+        const long long M = (long long)n * d * h * w, rpb = 4096;
+        k_bias_grad<<<(unsigned)((M + rpb - 1) / rpb), 128, 0, S(stream)>>>(static_cast<const bf16*>(dy), M, cout,
+                                                                              dbias, rpb);
+        return check(cudaGetLastError(), "k_bias_grad launch");
+    }
     const long long M = (long long)n * d * h * w;
     const int K = 27 * cin;
     const long long vpb = 8192;
@@ -536,7 +548,7 @@ extern "C" int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, 
         case 12: go(k_wgrad<12>); break;
         default: go(k_wgrad<16>); break;
     }
-    int rc = check(cudaGetLastError(), "k_wgrad launch");
+    rc = check(cudaGetLastError(), "k_wgrad launch");
     if (rc || !dbias) return rc;
     const long long rpb = 4096;
     k_bias_grad<<<(unsigned)((M + rpb - 1) / rpb), 128, 0, S(stream)>>>(static_cast<const bf16*>(dy), M, cout, dbias,

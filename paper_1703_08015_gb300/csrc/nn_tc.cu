@@ -442,6 +442,190 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
     }
 }
 
+// ---- weight gradient on the tensor cores ------------------------------------
+//
+// dw[tap][ci][co] = sum_p x[p + off(tap)][ci] dy[p][co] as 27 K-major GEMMs
+// over voxels.  x and dy are first packed channel-major over a padded grid
+// (D + 2) x (H + 2) x Wp, Wp >= W + 2 a multiple of 8: padded voxel q holds x
+// at q minus one voxel on each axis (wrapped on periodic axes, zero outside),
+// dy only at interior voxels (zero on the padding).  With flat indices, the
+// voxel p + off(tap) is q + dz Hp Wp + dy Wp + dx; the dz and dy parts are
+// multiples of 8 values (16 bytes), and dx in {-1, 0, 1} is taken from one of
+// three copies of packed x shifted by one value, so every operand row starts
+// 16-byte aligned.  Rows are Lp values long, the data G values in, with zero
+// guards of G values (G > Hp Wp + Wp) before and after.
+//
+//   xp[(dx + 1) Cp + ci][G + q] = xpad[ci][q + dx],   dyp[co][G + q] = dypad[co][q]
+//
+// with Cp the input channels rounded up to 16 (the rows past Cin zero).
+constexpr int WG_STAGES = 3;
+
+// One block per padded row (sample, z, y): the row's values go through shared
+// memory ([voxel][channel], an odd number of 32-bit words per voxel so that
+// the channel-major reads do not collide in banks) and out channel-major,
+// one warp per output row.  x has Cin channels, written as Cp >= Cin rows per
+// copy (the rows past Cin zero).
+__host__ __device__ constexpr int wg_pack_stride(int c) { return 2 * (((c + 1) / 2) | 1); }
+
+__global__ void k_wgrad_pack(const bf16* __restrict__ x, const bf16* __restrict__ dy, int D, int H, int W, int Cin,
+                             int Cp, int Cout, int wrap, int Hp, int Wp, long long G, long long Lp, bf16* __restrict__ xp,
+                             bf16* __restrict__ dyp) {
+    extern __shared__ __align__(16) unsigned char pack_smem[];
+    const int sx = wg_pack_stride(Cp), sd = wg_pack_stride(Cout);
+    bf16* xs = reinterpret_cast<bf16*>(pack_smem);
+    bf16* ds = xs + (size_t)Wp * sx;
+    const long long r = blockIdx.x;  // padded row
+    const int Dp = D + 2;
+    const int yp = (int)(r % Hp), zp = (int)((r / Hp) % Dp);
+    const long long n = r / ((long long)Hp * Dp);
+    const bool wx = wrap & 1, wy = wrap & 2, wz = wrap & 4;
+    const int zs = halo_nb(zp - 1, D, wz), ys = halo_nb(yp - 1, H, wy);
+    const bool interior = zp >= 1 && zp <= D && yp >= 1 && yp <= H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bf16 z0 = __float2bfloat16(0.f);
+    for (int v = warp; v < Wp; v += nw) {
+        const int xs_ = halo_nb(v - 1, W, wx);
+        const bool in = (zs | ys | xs_) >= 0;
+        const bf16* src = x + (((n * D + zs) * H + ys) * W + xs_) * Cin;
+        for (int c = lane; c < Cp; c += 32) xs[(size_t)v * sx + c] = in && c < Cin ? src[c] : z0;
+        const bool din = interior && v >= 1 && v <= W;
+        const bf16* dsrc = dy + (((n * D + zp - 1) * H + yp - 1) * W + v - 1) * Cout;
+        for (int c = lane; c < Cout; c += 32) ds[(size_t)v * sd + c] = din ? dsrc[c] : z0;
+    }
+    __syncthreads();
+    const long long row0 = G + r * Wp;
+    for (int rc = warp; rc < 3 * Cp; rc += nw) {  // rc = (dx + 1) Cp + ci
+        const int sh = rc / Cp - 1, ci = rc - (sh + 1) * Cp;
+        bf16* dst = xp + (size_t)rc * Lp + row0;
+        for (int v = lane; v < Wp; v += 32) {
+            const int src = v + sh;
+            dst[v] = (src >= 0 && src < Wp) ? xs[(size_t)src * sx + ci] : z0;
+        }
+    }
+    for (int co = warp; co < Cout; co += nw) {
+        bf16* dst = dyp + (size_t)co * Lp + row0;
+        for (int v = lane; v < Wp; v += 32) dst[v] = ds[(size_t)v * sd + co];
+    }
+}
+
+// One block: 128 output channels (from blockIdx.z * 128; rows past Cout are
+// zero) x the input channels of TG taps (from blockIdx.y * TG), summed over
+// the voxel steps [blockIdx.x * spc, ..) of 64 values.  Each stage holds the
+// dy tile (A, 128 x 64) and the TG shifted x tiles (B, Cin x 64 each), K-major,
+// and feeds four MMAs per 256 accumulator columns (Cp columns per tap: the
+// taps' tiles form one operand of TG Cp rows); the three-stage ring and the
+// bounded waits are those of tc_pipeline.
+// The block's sums are added to dw atomically.
+__global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
+                                                  int Cp, int Cout, int Hp, int Wp, long long G, long long Lp,
+                                                  long long nsteps, long long spc, int TG, float* __restrict__ dw) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t mbar[WG_STAGES];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t0 = blockIdx.y * TG, ntap = 27 - t0 < TG ? 27 - t0 : TG;
+    const int m0 = blockIdx.z * TC_M;
+    const long long s0 = (long long)blockIdx.x * spc, s1 = s0 + spc < nsteps ? s0 + spc : nsteps;
+    const int nk = (int)(s1 - s0);
+    const uint32_t a_bytes = TC_M * TC_BK * 2, b_bytes = (uint32_t)Cp * TC_BK * 2;
+    const uint32_t stage_bytes = a_bytes + (uint32_t)TG * b_bytes;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(TG * Cp)) ncols <<= 1;
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, ncols);
+    if (tid == 0)
+        for (int s = 0; s < WG_STAGES; s++) tc::mbar_init(&mbar[s], 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int tpm = 256 / Cp;  // taps per MMA
+    bool ok = true;
+    // this thread's 16-byte segment g of rows r0, r0 + 16, ..: fixed bases,
+    // per tap one offset (the copy for dx and the dz, dy shift)
+    const int g = tid & 7, r0 = tid >> 3;
+    const uint32_t so = tc::tile_off(r0, g, TC_KGAP, TC_RGAP), so16 = 2 * TC_RGAP;  // + 16 rows
+    const bf16* xb = xp + (size_t)r0 * Lp + g * 8;
+    const bf16* ab = dyp + g * 8;
+    const long long copy = (long long)Cp * Lp, plane = (long long)Hp * Wp;
+    auto fill = [&](unsigned char* st, int kc) {
+        const long long q = G + (s0 + kc) * TC_BK;
+#pragma unroll
+        for (int j = 0; j < TC_M / 16; j++) {
+            const int co = m0 + r0 + 16 * j;
+            tc::cp_async16(st + so + j * so16, ab + (size_t)(co < Cout ? co : 0) * Lp + q, co < Cout);
+        }
+        unsigned char* sb = st + a_bytes + so;
+#pragma unroll 1
+        for (int t = 0; t < ntap; t++, sb += b_bytes) {
+            const int tap = t0 + t;
+            const bf16* src = xb + (tap % 3) * copy + (tap / 9 - 1) * plane + (long long)((tap / 3) % 3 - 1) * Wp + q;
+            for (int ci = r0, k = 0; ci < Cp; ci += 16, k++)
+                tc::cp_async16(sb + k * so16, src + (size_t)(ci - r0) * Lp, true);
+        }
+    };
+    for (int p = 0; p < WG_STAGES - 1; p++) {
+        if (p < nk) fill(smem + p * stage_bytes, p);
+        tc::cp_async_commit();
+    }
+    for (int kc = 0; kc < nk; kc++) {
+        const int s = kc % WG_STAGES;
+        unsigned char* st = smem + s * stage_bytes;
+        tc::cp_async_wait<WG_STAGES - 2>();
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(st);
+            // the taps' x tiles follow each other with the same 8-row stride:
+            // one MMA covers up to 256 / Cp taps (N = their Cp columns each)
+            for (int t = 0; t < ntap; t += tpm) {
+                const int nn = (ntap - t < tpm ? ntap - t : tpm) * Cp;
+                const uint32_t id = tc::idesc_bf16_f32(TC_M, nn);
+                const uint32_t b0 = a0 + a_bytes + (uint32_t)t * b_bytes;
+#pragma unroll
+                for (int j = 0; j < TC_BK / 16; j++)
+                    tc::mma_bf16(tmem + (uint32_t)(t * Cp), tc::smem_desc(a0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP),
+                                 tc::smem_desc(b0 + 2 * j * TC_KGAP, TC_KGAP, TC_RGAP), id, kc > 0 || j > 0);
+            }
+            tc::mma_commit(&mbar[s]);
+        }
+        const int nxt = kc + WG_STAGES - 1;
+        if (nxt < nk) {
+            const int r = nxt % WG_STAGES;
+            if (kc >= 1) ok &= tc::mbar_wait(&mbar[r], ((kc - 1) / WG_STAGES) & 1, TC_WAIT);
+            fill(smem + r * stage_bytes, nxt);
+        }
+        tc::cp_async_commit();
+    }
+    if (nk > 0) {
+        const int last = nk - 1;
+        bool done = tc::mbar_wait(&mbar[last % WG_STAGES], (last / WG_STAGES) & 1, TC_WAIT);
+        if (!done) done = tc::mbar_wait(&mbar[last % WG_STAGES], (last / WG_STAGES) & 1, TC_WAIT);
+        ok &= done;
+    }
+    tc::cp_async_wait<0>();
+    if (!ok && lane == 0) atomicAdd(&g_tc_timeouts, 1u);
+    tc::fence_after_sync();
+    const int co = m0 + warp * 32 + lane;
+    if (nk > 0)
+        for (int c0 = 0; c0 < ntap * Cp; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (!ok || co >= Cout) continue;
+            const int t = c0 / Cp, ci0 = c0 - t * Cp;  // Cp % 16 == 0: one tap per 16 columns
+            float* dst = dw + ((size_t)(t0 + t) * Cin + ci0) * Cout + co;
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (ci0 + k < Cin) atomicAdd(dst + (size_t)k * Cout, v[k]);
+        }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
 }  // namespace nn
 }  // namespace lbm
 
@@ -552,6 +736,73 @@ int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* 
         static_cast<bf16*>(y), y32);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_conv_halo launch");
+}
+}  // namespace nn
+}  // namespace lbm
+
+namespace lbm {
+namespace nn {
+// Packed operands of the tensor-core weight gradient: one buffer kept for the
+// process and grown on demand (calls on one stream reuse it in order).
+static unsigned char* g_wg_buf = nullptr;
+static size_t g_wg_bytes = 0;
+
+// dw += the weight gradient on the tensor cores (input channels padded to a
+// multiple of 16, 8 <= cin <= 256: below 8 the padding would multiply the
+// work); returns 1, launching nothing, for other shapes or when the packed
+// operands do not fit.
+int wgrad_tc(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout, int wrap, float* dw,
+             cudaStream_t s) {
+    const int cp = (cin + 15) / 16 * 16;
+    if (cin < 8 || cp > 256) return 1;
+    const int Dp = d + 2, Hp = h + 2, Wp = (w + 2 + 7) / 8 * 8;
+    const long long plane = (long long)Hp * Wp;
+    const long long G = (plane + Wp + 8 + 63) / 64 * 64;
+    const long long L = (long long)n * Dp * plane;
+    const long long nsteps = (L + TC_BK - 1) / TC_BK;
+    const long long Lp = 2 * G + nsteps * TC_BK;
+    const size_t rows = 3 * (size_t)cp + (size_t)cout;
+    const size_t bytes = rows * (size_t)Lp * 2;
+    const uint32_t pack_smem = (uint32_t)Wp * (uint32_t)(wg_pack_stride(cp) + wg_pack_stride(cout)) * 2;
+    if (pack_smem > 200u * 1024u || (long long)n * Dp * Hp > 0x7fffffff) return 1;
+    if (bytes > g_wg_bytes) {
+        if (g_wg_buf) cudaFree(g_wg_buf);
+        g_wg_buf = nullptr;
+        g_wg_bytes = 0;
+        if (cudaMalloc(&g_wg_buf, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g_wg_buf = nullptr;
+            return 1;  // no room: the gather kernel needs none
+        }
+        g_wg_bytes = bytes;
+    }
+    bf16* xpk = reinterpret_cast<bf16*>(g_wg_buf);
+    bf16* dypk = xpk + (size_t)3 * cp * Lp;
+    cudaError_t e = cudaMemset2DAsync(g_wg_buf, (size_t)Lp * 2, 0, (size_t)G * 2, rows, s);
+    if (e == cudaSuccess)
+        e = cudaMemset2DAsync(g_wg_buf + (size_t)(G + L) * 2, (size_t)Lp * 2, 0, (size_t)(Lp - G - L) * 2, rows, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset2DAsync (weight-gradient guards)");
+    int rc = tc_launch_ok((const void*)k_wgrad_pack, pack_smem, "cudaFuncSetAttribute(k_wgrad_pack)");
+    if (rc) return rc;
+    k_wgrad_pack<<<(unsigned)(n * (long long)Dp * Hp), 256, pack_smem, s>>>(
+        static_cast<const bf16*>(x), static_cast<const bf16*>(dy), d, h, w, cin, cp, cout, wrap, Hp, Wp, G, Lp, xpk, dypk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_wgrad_pack launch");
+    // taps per block: the stage (dy tile + TG x tiles) within 72 KB, TG Cin <= 448 TMEM columns
+    const int TG = 448 / cp < 27 ? 448 / cp : 27;
+    const int groups = (27 + TG - 1) / TG, mt = (cout + TC_M - 1) / TC_M;
+    long long chunks = sm_count() / (groups * mt);
+    if (chunks < 1) chunks = 1;
+    if (chunks > nsteps) chunks = nsteps;
+    const long long spc = (nsteps + chunks - 1) / chunks;
+    chunks = (nsteps + spc - 1) / spc;
+    const uint32_t smem = WG_STAGES * (uint32_t)(TC_M * TC_BK * 2 + TG * cp * TC_BK * 2);
+    rc = tc_launch_ok((const void*)k_wgrad_tc, smem, "cudaFuncSetAttribute(k_wgrad_tc)");
+    if (rc) return rc;
+    k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), 128, smem, s>>>(xpk, dypk, cin, cp, cout, Hp, Wp,
+                                                                                       G, Lp, nsteps, spc, TG, dw);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_wgrad_tc launch");
 }
 }  // namespace nn
 }  // namespace lbm

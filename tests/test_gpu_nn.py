@@ -130,6 +130,44 @@ def test_conv_weight_gradient(nn, case):
     assert np.allclose(f64(db) + 0.5, ref_b, rtol=1e-5, atol=1e-4)
 
 
+# shapes of the tcgen05 weight gradient: ragged rows, every periodic
+# combination, channel counts off a multiple of 16 or of 8 (the input padded
+# to 16), several tap groups (cin 48 .. 192), two output-
+# channel tiles (cout 192 above), many voxel chunks (the last case)
+WGRAD_TC_CASES = [
+    (1, 3, 4, 6, 8, 16, 1),
+    (2, 3, 4, 5, 16, 4, 6),
+    (1, 2, 4, 4, 9, 9, 5),
+    (2, 6, 7, 9, 16, 32, 3),
+    (1, 5, 3, 13, 16, 16, 7),
+    (2, 3, 5, 6, 48, 48, 5),
+    (1, 8, 8, 8, 64, 128, 6),
+    (2, 4, 6, 8, 128, 64, 1),
+    (1, 4, 4, 4, 192, 16, 0),
+    (4, 16, 16, 16, 16, 32, 1),
+]
+
+
+@pytest.mark.parametrize("case", WGRAD_TC_CASES)
+def test_conv_weight_gradient_tcgen05(nn, case):
+    """The weight gradient on the tensor cores (channel-major packed operands,
+    one GEMM per tap) against the FP64 reference, accumulating into dw."""
+    n, d, h, w, cin, cout, wrap = case
+    rng = np.random.default_rng(13 + hash(case) % 2**31)
+    x = rand_bf16(rng, (n, d, h, w, cin))
+    dy = rand_bf16(rng, (n, d, h, w, cout))
+    dw = torch.full((27 * cin * cout,), 0.25, dtype=torch.float32, device="cuda")
+    db = torch.full((cout,), -0.5, dtype=torch.float32, device="cuda")
+    nn.lbm_nn_conv3d_wgrad(bf16_dev(x), bf16_dev(dy), n, d, h, w, cin, cout, wrap, dw, db)
+    torch.cuda.synchronize()
+    assert nn.lbm_nn_tc_timeouts() == 0
+    ref_w, ref_b = R.conv3d_bwd_weight(x, dy, wrap)
+    tol_w = 2.0 ** -16 * R.conv3d_bwd_weight(np.abs(x), np.abs(dy), wrap)[0] + 1e-6
+    err = np.abs(f64(dw).reshape(27, cin, cout) - 0.25 - ref_w)
+    assert np.all(err <= tol_w), float(np.max(err / tol_w))
+    assert np.allclose(f64(db) + 0.5, ref_b, rtol=1e-5, atol=1e-4)
+
+
 @pytest.mark.parametrize("entry", ["auto", "tc"])
 def test_large_conv_spans_many_tiles(nn, entry):
     """A 4 x 16^3 batch with 16 -> 64 channels (128 halo-tile blocks); every
