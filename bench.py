@@ -597,8 +597,9 @@ CONV_LAYERS = [(64, 16, 16), (64, 48, 16), (32, 16, 32), (32, 32, 32), (32, 96, 
 
 def run_conv(args):
     """Time the network's convolutions through lbm_nn_conv3d (kernel picked by
-    shape) and, where the shape allows, lbm_nn_conv3d_tc (tcgen05); one JSON
-    line with TFLOP/s per layer."""
+    shape) and, where the shape allows, lbm_nn_conv3d_tc (tcgen05), and their
+    weight gradients (lbm_nn_conv3d_wgrad); one JSON line with TFLOP/s per
+    layer."""
     import torch
 
     from paper_1703_08015_gb300 import nn
@@ -623,6 +624,20 @@ def run_conv(args):
             ms = e0.elapsed_time(e1) / reps
             row[name + "_us"] = ms * 1e3
             row[name + "_tflops"] = 2.0 * batch * side ** 3 * 27 * cin * cout / ms / 1e9
+        # the weight gradient of the same layer (dy shaped like y, FP32 accumulators)
+        dw = torch.zeros(27 * cin * cout, device="cuda")
+        for _ in range(3):
+            nn.lbm_nn_conv3d_wgrad(x, y, batch, side, side, side, cin, cout, 1, dw, None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            nn.lbm_nn_conv3d_wgrad(x, y, batch, side, side, side, cin, cout, 1, dw, None)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        row["wgrad_us"] = ms * 1e3
+        row["wgrad_tflops"] = 2.0 * batch * side ** 3 * 27 * cin * cout / ms / 1e9
         rows.append(row)
     print(json.dumps({"metric": "warm-start U-Net 3x3x3 convolution TFLOP/s (BF16, FP32 accumulation)",
                       "unit": "TFLOP/s", "dtype": "bf16", "data": "synthetic", "layers": rows,
