@@ -483,39 +483,62 @@ __global__ void k_wgrad_pack(const bf16* __restrict__ x, const bf16* __restrict_
     const bool interior = zp >= 1 && zp <= D && yp >= 1 && yp <= H;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const bf16 z0 = __float2bfloat16(0.f);
-    for (int v = warp; v < Wp; v += nw) {
+    // one 16-byte load per 8 channels where the channel count and alignment
+    // allow (every load of the block in flight at once), else one per value
+    auto load_row = [&](const bf16* base, int C, int Cw, bf16* dst, int sdst, bool vec, auto src_ok) {
+        if (vec) {
+            const int g8 = Cw / 8;
+            for (int e = threadIdx.x; e < Wp * g8; e += blockDim.x) {
+                const int v = e / g8, c8 = e - v * g8;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                const long long off = src_ok(v);
+                if (off >= 0 && c8 * 8 < C) val = *reinterpret_cast<const uint4*>(base + off * C + c8 * 8);
+                const bf16* h8 = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+                for (int k = 0; k < 8; k++) dst[(size_t)v * sdst + c8 * 8 + k] = h8[k];
+            }
+        } else {
+            for (int e = threadIdx.x; e < Wp * Cw; e += blockDim.x) {
+                const int v = e / Cw, c = e - v * Cw;
+                const long long off = src_ok(v);
+                dst[(size_t)v * sdst + c] = (off >= 0 && c < C) ? base[off * C + c] : z0;
+            }
+        }
+    };
+    const long long xrow = ((n * D + zs) * H + ys) * W;  // voxel index of (zs, ys, 0)
+    load_row(x, Cin, Cp, xs, sx, Cin % 8 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0, [&](int v) -> long long {
         const int xs_ = halo_nb(v - 1, W, wx);
-        const bool in = (zs | ys | xs_) >= 0;
-        const bf16* src = x + (((n * D + zs) * H + ys) * W + xs_) * Cin;
-        for (int c = lane; c < Cp; c += 32) xs[(size_t)v * sx + c] = in && c < Cin ? src[c] : z0;
-        const bool din = interior && v >= 1 && v <= W;
-        const bf16* dsrc = dy + (((n * D + zp - 1) * H + yp - 1) * W + v - 1) * Cout;
-        for (int c = lane; c < Cout; c += 32) ds[(size_t)v * sd + c] = din ? dsrc[c] : z0;
-    }
+        return (zs | ys | xs_) >= 0 ? xrow + xs_ : -1;
+    });
+    const long long drow = ((n * D + zp - 1) * H + yp - 1) * W;
+    load_row(dy, Cout, Cout, ds, sd, Cout % 8 == 0 && (reinterpret_cast<uintptr_t>(dy) & 15) == 0,
+             [&](int v) -> long long { return interior && v >= 1 && v <= W ? drow + v - 1 : -1; });
     __syncthreads();
+    // two values per 32-bit store (rows start at even offsets: G, Lp, Wp even)
     const long long row0 = G + r * Wp;
+    const int wh = Wp / 2;
     for (int rc = warp; rc < 3 * Cp; rc += nw) {  // rc = (dx + 1) Cp + ci
         const int sh = rc / Cp - 1, ci = rc - (sh + 1) * Cp;
-        bf16* dst = xp + (size_t)rc * Lp + row0;
-        for (int v = lane; v < Wp; v += 32) {
-            const int src = v + sh;
-            dst[v] = (src >= 0 && src < Wp) ? xs[(size_t)src * sx + ci] : z0;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(xp + (size_t)rc * Lp + row0);
+        for (int vp = lane; vp < wh; vp += 32) {
+            const int s0 = 2 * vp + sh, s1 = s0 + 1;
+            __nv_bfloat162 pr;
+            pr.x = (s0 >= 0 && s0 < Wp) ? xs[(size_t)s0 * sx + ci] : z0;
+            pr.y = (s1 >= 0 && s1 < Wp) ? xs[(size_t)s1 * sx + ci] : z0;
+            dst[vp] = *reinterpret_cast<const uint32_t*>(&pr);
         }
     }
     for (int co = warp; co < Cout; co += nw) {
-        bf16* dst = dyp + (size_t)co * Lp + row0;
-        for (int v = lane; v < Wp; v += 32) dst[v] = ds[(size_t)v * sd + co];
+        uint32_t* dst = reinterpret_cast<uint32_t*>(dyp + (size_t)co * Lp + row0);
+        for (int vp = lane; vp < wh; vp += 32) {
+            __nv_bfloat162 pr;
+            pr.x = ds[(size_t)(2 * vp) * sd + co];
+            pr.y = ds[(size_t)(2 * vp + 1) * sd + co];
+            dst[vp] = *reinterpret_cast<const uint32_t*>(&pr);
+        }
     }
 }
 
-// One block: 128 output channels (from blockIdx.z * 128; rows past Cout are
-// zero) x the input channels of TG taps (from blockIdx.y * TG), summed over
-// the voxel steps [blockIdx.x * spc, ..) of 64 values.  Each stage holds the
-// dy tile (A, 128 x 64) and the TG shifted x tiles (B, Cin x 64 each), K-major,
-// and feeds four MMAs per 256 accumulator columns (Cp columns per tap: the
-// taps' tiles form one operand of TG Cp rows); the three-stage ring and the
-// bounded waits are those of tc_pipeline.
-// The block's sums are added to dw atomically.
 __global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
                                                   int Cp, int Cout, int Hp, int Wp, long long G, long long Lp,
                                                   long long nsteps, long long spc, int TG, float* __restrict__ dw) {
