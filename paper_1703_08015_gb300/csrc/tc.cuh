@@ -107,10 +107,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
-// 16-byte global -> shared copy completing asynchronously (cp.async, L1
-// allocating); `full` false writes 16 zero bytes without reading the source.
+// 16-byte global -> shared copy completing asynchronously (cp.async, cached
+// in L2 only: the blocks' shared memory leaves little L1); `full` false writes
+// 16 zero bytes without reading the source.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool full) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
                  "r"(full ? 16 : 0)
                  : "memory");
 }
