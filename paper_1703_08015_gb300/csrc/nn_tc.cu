@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
 //
 // with Cp the input channels rounded up to 16 (the rows past Cin zero).
 constexpr int WG_STAGES = 3;
+constexpr int WG_THREADS = 256;  // two warps per TMEM lane quadrant
 
 // One block per padded row (sample, z, y): the row's values go through shared
 // memory ([voxel][channel], an odd number of 32-bit words per voxel so that
@@ -539,7 +540,7 @@ __global__ void k_wgrad_pack(const bf16* __restrict__ x, const bf16* __restrict_
     }
 }
 
-__global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
+__global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
                                                   int Cp, int Cout, int Hp, int Wp, long long G, long long Lp,
                                                   long long nsteps, long long spc, int TG, float* __restrict__ dw) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -563,9 +564,11 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, c
     const uint32_t tmem = tmem_slot;
     const int tpm = 256 / Cp;  // taps per MMA
     bool ok = true;
-    // this thread's 16-byte segment g of rows r0, r0 + 16, ..: fixed bases,
-    // per tap one offset (the copy for dx and the dz, dy shift)
-    const int g = tid & 7, r0 = tid >> 3;
+    // this thread's 16-byte segment g of rows r0, r0 + 16, .. (of the taps of
+    // its parity): fixed bases, per tap one offset (the copy for dx and the
+    // dz, dy shift)
+    const int th = tid & 127, par = tid >> 7;
+    const int g = th & 7, r0 = th >> 3;
     const uint32_t so = tc::tile_off(r0, g, TC_KGAP, TC_RGAP), so16 = 2 * TC_RGAP;  // + 16 rows
     const bf16* xb = xp + (size_t)r0 * Lp + g * 8;
     const bf16* ab = dyp + g * 8;
@@ -573,13 +576,13 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, c
     auto fill = [&](unsigned char* st, int kc) {
         const long long q = G + (s0 + kc) * TC_BK;
 #pragma unroll
-        for (int j = 0; j < TC_M / 16; j++) {
+        for (int j = par; j < TC_M / 16; j += 2) {
             const int co = m0 + r0 + 16 * j;
             tc::cp_async16(st + so + j * so16, ab + (size_t)(co < Cout ? co : 0) * Lp + q, co < Cout);
         }
-        unsigned char* sb = st + a_bytes + so;
+        unsigned char* sb = st + a_bytes + so + par * b_bytes;
 #pragma unroll 1
-        for (int t = 0; t < ntap; t++, sb += b_bytes) {
+        for (int t = par; t < ntap; t += 2, sb += 2 * b_bytes) {
             const int tap = t0 + t;
             const bf16* src = xb + (tap % 3) * copy + (tap / 9 - 1) * plane + (long long)((tap / 3) % 3 - 1) * Wp + q;
             for (int ci = r0, k = 0; ci < Cp; ci += 16, k++)
@@ -629,11 +632,13 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ xp, c
     tc::cp_async_wait<0>();
     if (!ok && lane == 0) atomicAdd(&g_tc_timeouts, 1u);
     tc::fence_after_sync();
-    const int co = m0 + warp * 32 + lane;
+    // warps w and w + 4 read the same TMEM lanes (32 (w % 4) ..), alternate chunks
+    const int quad = warp & 3;
+    const int co = m0 + quad * 32 + lane;
     if (nk > 0)
-        for (int c0 = 0; c0 < ntap * Cp; c0 += 16) {
+        for (int c0 = 16 * par; c0 < ntap * Cp; c0 += 32) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
             if (!ok || co >= Cout) continue;
             const int t = c0 / Cp, ci0 = c0 - t * Cp;  // Cp % 16 == 0: one tap per 16 columns
             float* dst = dw + ((size_t)(t0 + t) * Cin + ci0) * Cout + co;
@@ -822,7 +827,7 @@ int wgrad_tc(const void* x, const void* dy, int n, int d, int h, int w, int cin,
     const uint32_t smem = WG_STAGES * (uint32_t)(TC_M * TC_BK * 2 + TG * cp * TC_BK * 2);
     rc = tc_launch_ok((const void*)k_wgrad_tc, smem, "cudaFuncSetAttribute(k_wgrad_tc)");
     if (rc) return rc;
-    k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), 128, smem, s>>>(xpk, dypk, cin, cp, cout, Hp, Wp,
+    k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), WG_THREADS, smem, s>>>(xpk, dypk, cin, cp, cout, Hp, Wp,
                                                                                        G, Lp, nsteps, spc, TG, dw);
     e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_wgrad_tc launch");
