@@ -75,7 +75,7 @@ def build(verbose: bool = False, extra=(), jobs: int = None) -> str:
                 print(f"[{os.path.basename(o)}]\n{log}", file=sys.stderr)
     if _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"linking failed:\n{' '.join(cmd)}\n{r.stdout}{r.stderr}")

@@ -16,10 +16,36 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 
 #include "internal.h"
 
 namespace lbm {
+
+// f(begin, end) over [0, n) in up to 16 host threads (each range a contiguous
+// block of items; the caller's results depend only on the item, not on the
+// split).  Runs serially for small n or when threads cannot be started.
+template <class F>
+static void parallel_ranges(int64_t n, int64_t min_per_thread, F f) {
+    const unsigned hc = std::thread::hardware_concurrency();
+    int64_t t = std::min<int64_t>(hc ? std::min(hc, 16u) : 1u, n / std::max<int64_t>(min_per_thread, 1));
+    if (t <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    const int64_t chunk = (n + t - 1) / t;
+    std::vector<std::thread> pool;
+    int64_t done = 0;  // items handed to started threads
+    try {
+        for (int64_t b = 0; b < n; b += chunk) {
+            pool.emplace_back(f, b, std::min(n, b + chunk));
+            done = std::min(n, b + chunk);
+        }
+    } catch (...) {
+    }
+    for (auto& th : pool) th.join();
+    if (done < n) f(done, n);  // threads could not be started: finish here
+}
 
 static thread_local char g_err[512] = "";
 
@@ -98,13 +124,16 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     T->tmask.clear();
     T->coords.clear();
 
-    int32_t count = 0;
-    int64_t n_fluid = 0;
-    std::vector<uint64_t> bits(T->words);
-    for (int tz = 0; tz < ntz; tz++)
-        for (int ty = 0; ty < nty; ty++)
+    // fluid bits and counts of every tile, tile rows (tz, ty) in parallel
+    const int W = T->words;
+    std::vector<uint64_t> all_bits((size_t)n_tiles64 * W, 0ull);
+    std::vector<int32_t> all_nf((size_t)n_tiles64, 0);
+    parallel_ranges((int64_t)ntz * nty, 8, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; r++) {
+            const int tz = (int)(r / nty), ty = (int)(r % nty);
             for (int tx = 0; tx < ntx; tx++) {
-                std::fill(bits.begin(), bits.end(), 0ull);
+                const size_t t = ((size_t)tz * nty + ty) * ntx + tx;
+                uint64_t* bits = &all_bits[t * W];
                 int nf = 0;
                 for (int lz = 0; lz < az; lz++) {
                     const int z = tz * az + lz;
@@ -124,20 +153,37 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
                         }
                     }
                 }
-                if (nf) {
-                    T->tile_map[((size_t)tz * nty + ty) * ntx + tx] = count++;
-                    T->tmask.insert(T->tmask.end(), bits.begin(), bits.end());
-                    T->coords.push_back(tx);
-                    T->coords.push_back(ty);
-                    T->coords.push_back(tz);
-                    n_fluid += nf;
-                }
+                all_nf[t] = nf;
             }
+        }
+    });
+    // ranks in row-major scan order (serial: the tile index is a prefix count)
+    int32_t count = 0;
+    int64_t n_fluid = 0;
+    for (int tz = 0; tz < ntz; tz++)
+        for (int ty = 0; ty < nty; ty++)
+            for (int tx = 0; tx < ntx; tx++) {
+                const size_t t = ((size_t)tz * nty + ty) * ntx + tx;
+                if (!all_nf[t]) continue;
+                T->tile_map[t] = count++;
+                n_fluid += all_nf[t];
+            }
+    T->tmask.resize((size_t)count * W);
+    T->coords.resize((size_t)count * 3);
+    for (size_t t = 0; t < (size_t)n_tiles64; t++) {
+        const int32_t k = T->tile_map[t];
+        if (k < 0) continue;
+        std::memcpy(&T->tmask[(size_t)k * W], &all_bits[t * W], (size_t)W * sizeof(uint64_t));
+        T->coords[(size_t)3 * k] = (int)(t % ntx);
+        T->coords[(size_t)3 * k + 1] = (int)((t / ntx) % nty);
+        T->coords[(size_t)3 * k + 2] = (int)(t / ((size_t)ntx * nty));
+    }
 
     const int per[3] = {p->periodic[0] ? 1 : 0, p->periodic[1] ? 1 : 0, d == 3 && p->periodic[2] ? 1 : 0};
     const int ntv[3] = {ntx, nty, ntz};
     T->nbr.resize((size_t)count * T->nn);
-    for (int32_t k = 0; k < count; k++) {
+    parallel_ranges(count, 1024, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; k++) {
         const int* c = &T->coords[(size_t)3 * k];
         int slot = 0;
         for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
@@ -157,6 +203,7 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
                         ok ? T->tile_map[((size_t)q[2] * nty + q[1]) * ntx + q[0]] : -1;
                 }
     }
+    });
 
     // Compact layout: a tile stores only its fluid nodes, in row order, link
     // after link with no padding (contiguous link arrays fill whole sectors).
@@ -263,26 +310,39 @@ void build_work_list(HostTiling* T, int threads, int max_tiles) {
     const int32_t n = T->info.n_ftiles;
     T->nodes.clear();
     T->blocks.clear();
-    T->nodes.reserve((size_t)T->info.n_fluid);
-    WorkBlock cur{0, 0, 0, 0};
+    // first node of every tile (a prefix count), then the block boundaries
+    std::vector<int64_t> first((size_t)n + 1, 0);
     for (int32_t k = 0; k < n; k++) {
         const uint64_t* m = &T->tmask[(size_t)k * T->words];
         int nf = 0;
         for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(m[w]);
+        first[k + 1] = first[k] + nf;
+    }
+    WorkBlock cur{0, 0, 0, 0};
+    for (int32_t k = 0; k < n; k++) {
+        const int nf = (int)(first[k + 1] - first[k]);
         if (cur.n_tiles > 0 && (cur.count + nf > threads || cur.n_tiles == max_tiles)) {
             T->blocks.push_back(cur);
             cur = WorkBlock{0, 0, 0, 0};
         }
         if (cur.n_tiles == 0) {
-            cur.node_begin = (int)T->nodes.size();
+            cur.node_begin = (int)first[k];
             cur.tile_begin = k;
         }
-        for (int node = 0; node < nt; node++)
-            if ((m[node >> 6] >> (node & 63)) & 1ull) T->nodes.push_back((uint32_t)k * (uint32_t)nt + node);
         cur.count += nf;
         cur.n_tiles++;
     }
     if (cur.n_tiles > 0) T->blocks.push_back(cur);
+    // the nodes of each tile in row order, tiles in parallel
+    T->nodes.resize((size_t)first[n]);
+    parallel_ranges(n, 1024, [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; k++) {
+            const uint64_t* m = &T->tmask[(size_t)k * T->words];
+            uint32_t* out = &T->nodes[(size_t)first[k]];
+            for (int node = 0; node < nt; node++)
+                if ((m[node >> 6] >> (node & 63)) & 1ull) *out++ = (uint32_t)k * (uint32_t)nt + node;
+        }
+    });
 }
 
 }  // namespace lbm
