@@ -154,6 +154,9 @@ typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library */
  *             a non-periodic edge (the 3^3 tile bitmap of Fig. 5); NULL =
  *             not wanted.  Its size is only known after a size query.
  *   out       host out, the counts and the bytes of one PDF copy.
+ * The mask scan and the neighbour records run over tile rows in up to 16
+ * host threads (the result does not depend on their number); lbm_init tiles
+ * the same way.
  * Errors: LBM_ERR_ARG (NULL mask/out/p, bad sizes or tile edge),
  * LBM_ERR_SHAPE (periodic axis not a multiple of tile_a). */
 int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask,
