@@ -540,6 +540,16 @@ __global__ void k_wgrad_pack(const bf16* __restrict__ x, const bf16* __restrict_
     }
 }
 
+// One block: 128 output channels (from blockIdx.z * 128; rows past Cout are
+// zero) x the Cp columns of each of TG taps (from blockIdx.y * TG), summed
+// over the voxel steps [blockIdx.x * spc, ..) of 64 values.  Each stage holds
+// the dy tile (A, 128 x 64) and the TG shifted x tiles (B, Cp x 64 each),
+// K-major; the x tiles lie back to back with one 8-row stride, so one MMA
+// covers up to 256 / Cp taps, one TMEM accumulator column range per tap.  The
+// two warps of each TMEM lane quadrant split the fills (taps of one parity
+// each) and the epilogue's column chunks; the three-stage ring and the bounded
+// waits are those of tc_pipeline.  The block's sums are added to dw
+// atomically.
 __global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
                                                   int Cp, int Cout, int Hp, int Wp, long long G, long long Lp,
                                                   long long nsteps, long long spc, int TG, float* __restrict__ dw) {
