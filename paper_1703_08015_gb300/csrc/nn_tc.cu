@@ -1,8 +1,9 @@
 // nn_tc.cu -- GEMMs of the learned warm start on the 5th-generation tensor
 // cores (tcgen05): operands staged in shared memory by the block's threads,
 // the FP32 accumulator in tensor memory (TMEM), one thread issuing the MMAs
-// and an mbarrier reporting their completion.  A plain BF16 GEMM and the
-// 3x3x3 convolution as an implicit GEMM share one pipeline.  See
+// and an mbarrier reporting their completion.  A plain BF16 GEMM, the 3x3x3
+// convolution (as an implicit GEMM, and reading a shared-memory halo tile)
+// and its weight gradient (one GEMM per tap over packed operands).  See
 // include/lbm_nn.h.
 #include <cuda_bf16.h>
 
@@ -714,8 +715,6 @@ int conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wg
 
 namespace lbm {
 namespace nn {
-// The halo-tile tensor-core convolution (cin % 16 == 0, cout % 16 == 0,
-// 16-byte aligned operands); returns 1, launching nothing, for other shapes.
 static int g_halo_mb = 0, g_halo_nt = 0;  // fixed by lbm_nn_conv_tune; 0 = chosen per shape
 
 static int sm_count() {
@@ -730,6 +729,8 @@ static int sm_count() {
     return sms;
 }
 
+// The halo-tile tensor-core convolution (cin % 16 == 0, cout % 16 == 0,
+// 16-byte aligned operands); returns 1, launching nothing, for other shapes.
 int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
                 int relu, int wrap, void* y, float* y32, cudaStream_t s) {
     if (cin % 16 || cout % 16 || ((uintptr_t)x | (uintptr_t)wgt | (uintptr_t)y | (uintptr_t)y32) & 15) return 1;
