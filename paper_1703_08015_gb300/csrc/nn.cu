@@ -1,7 +1,8 @@
 // nn.cu -- kernels of the learned warm start (not in the paper): 3x3x3
 // convolutions as implicit GEMMs on tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation), their backward passes, and the elementwise
-// steps of training.  See include/lbm_nn.h.
+// operands, FP32 accumulation) for the shapes the tcgen05 kernels of
+// nn_tc.cu do not take, their backward passes, the dispatch between the two,
+// and the elementwise steps of training.  See include/lbm_nn.h.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -148,7 +149,9 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N,
 
 // dW[(tap,ci)][co] += sum_p x[p + off(tap)][ci] dy[p][co]: GEMM with 64 rows of
 // (tap, ci) per block, NF*8 output channels from blockIdx.z * NF*8, split over
-// voxel chunks (blockIdx.y) whose partial sums are added atomically.
+// voxel chunks (blockIdx.y) whose partial sums are added atomically.  The
+// gather form, for the shapes the tcgen05 weight gradient does not take
+// (fewer than 8 input channels, more than 256).
 template <int NF>
 __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int N,
                                                int D, int H, int W, int Cin, int Cout, int wrap,
