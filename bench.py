@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="d3q19_spheres_256")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--arith", default="auto", choices=["auto", "f64", "fixed", "ff"])
+    ap.add_argument("--arith", default="auto", choices=["auto", "f64", "fixed", "ff", "ff_table"],
+                    help="FP64 arithmetic: auto = ff, the staged tile-map step; ff_table = the per-node "
+                         "gather table (the connectivity-matrix scheme of Sec. 2.3.1)")
     ap.add_argument("--storage", default="f64", choices=["f64", "f32", "f32s", "f16s"])
     ap.add_argument("--layout", default="t2c", choices=["t2c", "tgb"],
                     help="two PDF copies (T2C) or one copy with ghost buffers (TGB)")
@@ -108,49 +110,75 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a window."""
+CLOCK_Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+def _clock_rows(text):
+    """(sm MHz, max MHz, active reasons) per nvidia-smi CSV row of CLOCK_Q."""
+    out = []
+    for r in csv.reader(io.StringIO(text)):
+        if len(r) < 10:
+            continue
+        try:
+            sm, smax = float(r[2]), float(r[3])
+        except ValueError:
+            continue
+        out.append((sm, smax, {n for k, n in enumerate(CLOCK_REASONS) if r[6 + k].strip().lower() == "active"}))
+    return out
+
+
+def clock_snapshot(gpu_index):
+    """One read-only nvidia-smi query of the SM clock and throttle reasons."""
+    try:
+        r = subprocess.run(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                            "-i", str(gpu_index)], capture_output=True, text=True, timeout=20)
+        return _clock_rows(r.stdout)
+    except (OSError, subprocess.SubprocessError):
+        return []
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons around and during a
+    window: one query just before it starts, a 20 ms sampling loop while it
+    runs, one query just after it ends (all read-only)."""
 
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
+        self.before = clock_snapshot(gpu_index)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                ["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits", "-lms", "20",
                  "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # the sampler is up before the window opens
         except OSError:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
+        during = []
+        if self.proc is not None:
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            during = _clock_rows(out)
+        after = clock_snapshot(self.gpu)
+        rows = self.before + during + after
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        self.proc.terminate()
-        out, _ = self.proc.communicate(timeout=10)
-        rows = list(csv.reader(io.StringIO(out)))
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 10:
-                continue
-            try:
-                sm.append(float(r[2]))
-                smax = float(r[3])
-            except ValueError:
-                continue
-            for k, n in enumerate(names):
-                if r[6 + k].strip().lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set().union(*(r[2] for r in rows))
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[-1][1],
+                "reasons": sorted(reasons), "samples": len(rows), "samples_during": len(during),
+                "sm_mhz_before": self.before[0][0] if self.before else None,
+                "sm_mhz_after": after[0][0] if after else None,
+                "how": "nvidia-smi query just before and just after the timed region, -lms 20 loop during it"}
 
 
 STEP_SOURCES = {  # the sources each step kernel is built from
     "common": ("internal.h", "lattice.cuh", "tile.cuh", "tiling.cpp"),
-    "ff": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
+    "ff_staged": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
+    "ff_table_cm": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
     "fixed": ("collide_f64.cuh", "step_fixed.cu"),
     "f64": ("collide_f64.cuh", "step_f64.cu"),
     "f32": ("collide_f32.cuh", "step_f32.cu"),
@@ -195,6 +223,23 @@ def committed_traffic(workload, arith):
     if not e or e.get("kernel_source_sha") != kernel_source_sha(kind):
         return None, None
     return e.get("dram_bytes_per_launch"), e.get("note")
+
+
+def step_kernel_name(lat, a, storage, layout, arith_name):
+    """The step kernel a bench line times, with the form of its gather."""
+    lt = "D3Q19" if lat == 19 else "D2Q9"
+    if layout == "tgb":
+        return f"k_step_tgb<{lt},{a}> (single copy with ghost buffers, Fig. 4 layout, pull form)"
+    if storage != "f64":
+        store = {"f32": "StoreF32", "f32s": "StoreF32S", "f16s": "StoreF16S"}[storage]
+        return (f"k_step_f32<{lt},{a},{store}> (tile-map T2C step of Fig. 5: neighbourhood staged per "
+                "block; FP32 collision)")
+    return {"ff_staged": f"k_step_ff<{lt},{a}> (tile-map T2C step of Fig. 5: neighbourhood staged per block; "
+                         "float-float FP64 update)",
+            "ff_table_cm": f"k_step_ff_table<{lt}> (per-node gather table built once: the connectivity-matrix "
+                           "scheme of Sec. 2.3.1 on compact tiles, not the tile-map method; float-float FP64)",
+            "fixed": f"k_step_fixed<{lt},{a}> (tile-map T2C step; 64-bit fixed-point FP64 update)",
+            "f64": f"k_step_f64<{lt},{a}> (tile-map T2C step; native FP64 update)"}[arith_name]
 
 
 def cpu_baseline(mask, params, seconds=10.0, min_steps=2):
@@ -280,7 +325,7 @@ def run_ours(args):
     mask, params, info = geo.workload(args.workload)
     lat, a = params["lattice"], params["tile_a"]
     arith = {"auto": lbm.LBM_ARITH_AUTO, "f64": lbm.LBM_ARITH_F64, "fixed": lbm.LBM_ARITH_FIXED,
-             "ff": lbm.LBM_ARITH_FF}[args.arith]
+             "ff": lbm.LBM_ARITH_FF, "ff_table": lbm.LBM_ARITH_FF_TABLE}[args.arith]
     storage = {"f64": lbm.LBM_STORE_F64, "f32": lbm.LBM_STORE_F32, "f32s": lbm.LBM_STORE_F32S,
                "f16s": lbm.LBM_STORE_F16S}[args.storage]
     layout = {"t2c": lbm.LBM_LAYOUT_T2C, "tgb": lbm.LBM_LAYOUT_TGB}[args.layout]
@@ -326,9 +371,10 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     step_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
     ms_max, value = replica_throughput(ms, n_fluid, args.steps, world, dev)
-    # "ff": float-float through the gather table (the default); "ff_staged": --arith ff
-    arith_name = {lbm.LBM_ARITH_AUTO: "ff", lbm.LBM_ARITH_FIXED: "fixed", lbm.LBM_ARITH_F64: "f64",
-                  lbm.LBM_ARITH_FF: "ff_staged"}[arith]
+    # "ff_staged": the float-float tile-map step (the default, --arith auto or ff);
+    # "ff_table_cm": the float-float step through the per-node gather table
+    arith_name = {lbm.LBM_ARITH_AUTO: "ff_staged", lbm.LBM_ARITH_FIXED: "fixed", lbm.LBM_ARITH_F64: "f64",
+                  lbm.LBM_ARITH_FF: "ff_staged", lbm.LBM_ARITH_FF_TABLE: "ff_table_cm"}[arith]
     tiling = solver.tiling
     solver.close()
     del solver
@@ -360,6 +406,8 @@ def run_ours(args):
                    "size": list(mask.shape[::-1]), "tile": a, "fluid_nodes": n_fluid, **tiling_stats,
                    "tau": params["tau"], "force": params["force"], "storage": args.storage,
                    "arith": arith_name if args.storage == "f64" else "f32",
+                   "gather_table_bytes": ((lat + 1) * 4 * n_fluid
+                                          if args.storage == "f64" and arith_name == "ff_table_cm" else 0),
                    "stats_every": STATS_EVERY, "parallelism": "replicas" if world > 1 else "single",
                    "layout": args.layout,
                    "pdf_device_bytes": dev_bytes,
@@ -371,7 +419,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "k_step (tiled stream+collide)", "bytes_per_launch": bytes_per_launch,
+                     "kernel": step_kernel_name(lat, a, args.storage, args.layout, arith_name),
+                     "bytes_per_launch": bytes_per_launch,
                      "step_kernel_ms": step_ms, "traffic_note": tnote},
         "issue_roofline": issue_roofline(args, arith_name, n_fluid, step_ms),
         "clocks": clocks,

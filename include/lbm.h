@@ -75,10 +75,15 @@ extern "C" {
 /* Arithmetic of the FP64 step.  All variants compute the same FP64 update;
  * they differ only in rounding (see lbm_step).  Nodes outside the range of
  * the fixed-point and float-float forms fall back to native FP64. */
-#define LBM_ARITH_AUTO   0 /* LBM_ARITH_FF, the sources read from a gather table (below) */
+#define LBM_ARITH_AUTO   0 /* LBM_ARITH_FF (the default) */
 #define LBM_ARITH_F64    1 /* native FP64 instructions */
 #define LBM_ARITH_FIXED  2 /* exact 64-bit fixed-point sums and products, no FP64 instructions */
-#define LBM_ARITH_FF     3 /* exact integer sums, float-float products (~48 bits), no FP64 instructions */
+#define LBM_ARITH_FF     3 /* exact integer sums, float-float products (~48 bits), no FP64 instructions;
+                              the tile-map gather of Fig. 5 (neighbourhood staged per block) */
+#define LBM_ARITH_FF_TABLE 4 /* LBM_ARITH_FF with each node's sources read from a per-node
+                              gather table built once: the connectivity-matrix scheme of
+                              Sec. 2.3.1 (Eqs. 13-14) on the compact tiles, not the tile-map
+                              method; 4 (q + 1) bytes per fluid node more per step */
 
 /* PDF layouts (Sec. 3.1).  T2C: two copies, each step reads one and writes the
  * other (Fig. 5).  TGB: one copy updated in place; values that cross a tile
@@ -191,12 +196,13 @@ int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
  * Asynchronous on `stream`.  With LBM_ARITH_FIXED the FP64 update is computed
  * with 64-bit fixed-point integers (resolution 2^-60), with LBM_ARITH_FF
  * with exact integer sums and float-float products; either is rounded once to
- * FP64 and agrees with LBM_ARITH_F64 to rounding.  LBM_ARITH_AUTO is the
- * float-float update with the gather resolved once: lbm_init builds a table
- * of every node's source slots (4 (q + 1) bytes per fluid node, allocated by
- * the library, T2C layout, when the copy's value indices fit int32; else the
- * staged gather of LBM_ARITH_FF), and the step reads it instead of staging
- * the neighbourhood.
+ * FP64 and agrees with LBM_ARITH_F64 to rounding.  LBM_ARITH_AUTO is
+ * LBM_ARITH_FF.  LBM_ARITH_FF_TABLE is the float-float update with the gather
+ * resolved once, the connectivity-matrix scheme the paper compares against
+ * (Sec. 2.3.1): lbm_init builds a table of every node's source slots
+ * (4 (q + 1) bytes per fluid node, allocated by the library, T2C layout,
+ * when the copy's value indices fit int32; else the staged gather of
+ * LBM_ARITH_FF), and the step reads it instead of staging the neighbourhood.
  * Errors: LBM_ERR_ARG (NULL ctx, nsteps < 0), LBM_ERR_CUDA. */
 int lbm_step(lbm_ctx* ctx, int nsteps, void* stream);
 
@@ -253,8 +259,11 @@ int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
  * tilings that need more than LBM_NOALLOC_MAX_BLOCKS blocks (more than
  * 262,144 non-empty 4^3 tiles, for example) are rejected with
  * LBM_ERR_CAPACITY.  The
- * first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * device that was current at lbm_init must be current (else LBM_ERR_ARG).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  A
+ * cudaDeviceReset invalidates that address: calls after one are not
+ * supported.  All
  * calls share the one array, which keeps the last call's contents: every
  * block writes its slots before they are read, so nothing has to start at
  * zero, but calls whose kernels overlap on the GPU race with each other.
@@ -316,6 +325,36 @@ int lbm_filter_period2(lbm_ctx* ctx, void* stream);
 /* lbm_export_pdfs for sample k of a batch (dense over that sample's box).
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 int lbm_export_pdfs_sample(lbm_ctx* ctx, int sample, double* pdfs, int flags, void* stream);
+
+/* ---- tile layers: the domain split across GPUs (not in the paper) ----------
+ * The paper names multi-GPU runs as future work (Sec. 5).  A geometry split
+ * into slabs of whole tile layers along its slowest tile axis (z in 3D, y in
+ * 2D) runs one context per GPU on the rank's box: its slab plus one ghost
+ * tile layer on each side that has a neighbour.  Tiles are numbered
+ * row-major with that axis slowest, so the non-empty tiles of a run of
+ * layers are consecutive and their values form one contiguous range of a
+ * PDF copy; the same layer of the same mask has the same bytes in any
+ * context.  After every step a rank copies its first and last interior
+ * layers into the neighbours' ghost layers (NCCL send/recv into the
+ * receiver's memory) and the split run matches the undivided one bit for
+ * bit.  Single-geometry T2C contexts only (LBM_ERR_ARG otherwise). */
+
+/* Byte offset and length, within either PDF copy, of the non-empty tiles of
+ * the tile layers [l_begin, l_end).  Host only, no device work.
+ * Errors: LBM_ERR_ARG (NULL arguments, layers out of range, batch or TGB). */
+int lbm_layer_range(const lbm_ctx* ctx, int l_begin, int l_end, size_t* offset, size_t* bytes);
+
+/* Which of the two PDF buffers given to lbm_init (0 = pdf_a, 1 = pdf_b)
+ * holds the current post-collision state, as of the work enqueued so far;
+ * -1 for NULL. */
+int lbm_current_copy(const lbm_ctx* ctx);
+
+/* lbm_moments' statistics restricted to the fluid nodes of the tile layers
+ * [l_begin, l_end) (a rank's interior), reduced in a fixed order; flags
+ * LBM_STATS_RESIDUAL as in lbm_moments (the saved velocity covers those
+ * layers).  Synchronises `stream`.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA,
+ * LBM_ERR_DIVERGED. */
+int lbm_moments_layers(lbm_ctx* ctx, int l_begin, int l_end, lbm_stats* stats, int flags, void* stream);
 
 /* Number of samples in the context (1 for lbm_init); 0 for NULL. */
 int lbm_num_samples(const lbm_ctx* ctx);

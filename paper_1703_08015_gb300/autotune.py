@@ -72,13 +72,16 @@ def time_mapping(masks, lattice, cfg, storage, periodic, tau, force, steps=40, d
 
 
 def tune(masks, lattice, storage=lbm.LBM_STORE_F32S, periodic=(1, 0, 0), tau=0.6, force=(1e-6, 0, 0),
-         steps=40, use_cache=True, device="cuda"):
-    """Returns (best mapping dict, {mapping: MLUPS} of every candidate tried)."""
+         steps=40, use_cache=True, device="cuda", cache_path=None):
+    """Returns (best mapping dict, {mapping: MLUPS} of every candidate tried).
+    The choice is cached in `cache_path` (default _build/autotune.json) under
+    the GPU / lattice / storage / workload key and reused by later calls."""
+    cache_path = cache_path or CACHE
     masks = [np.ascontiguousarray(m[None] if m.ndim == 2 else m, np.uint8) for m in masks]
     key = _signature(lattice, storage, masks)
     cache = {}
-    if use_cache and os.path.exists(CACHE):
-        with open(CACHE) as f:
+    if use_cache and os.path.exists(cache_path):
+        with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
             return cache[key]["best"], cache[key]["trials"]
@@ -90,7 +93,7 @@ def tune(masks, lattice, storage=lbm.LBM_STORE_F32S, periodic=(1, 0, 0), tau=0.6
     a, bn, pe = best_name[1:].split("_")
     best = {"tile_a": int(a), "block_nodes": int(bn[1:]), "persistent": int(pe[1:])}
     cache[key] = {"best": best, "trials": trials, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
-    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-    with open(CACHE, "w") as f:
+    os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+    with open(cache_path, "w") as f:
         json.dump(cache, f, indent=1)
     return best, trials

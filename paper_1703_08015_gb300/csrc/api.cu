@@ -22,7 +22,8 @@ StepLaunch select_step(const lbm_params* p) {
         StepLaunch f = nullptr;
         if (arith == LBM_ARITH_F64) return select_step_f64(lattice, a, model, storage);
         if (arith == LBM_ARITH_FIXED) f = select_step_fixed(lattice, a, model);
-        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO) f = select_step_ff(lattice, a, model);
+        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO || arith == LBM_ARITH_FF_TABLE)
+            f = select_step_ff(lattice, a, model);
         return f ? f : select_step_f64(lattice, a, model, storage);
     }
     return select_step_f32(lattice, a, model, storage, p->block_nodes, p->persistent);
@@ -70,6 +71,12 @@ struct lbm_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_pairs = 8;  // each graph replays 2 * graph_pairs steps
     bool use_graph = true;
+    int device = 0;       // the CUDA device current at lbm_init (the tables live there)
+    // single geometry: per layer of tiles along the slowest tile axis (z in 3D,
+    // y in 2D), the index of its first non-empty tile and the value offset of
+    // that tile's PDF block (entry n_layers: the totals)
+    std::vector<int> layer_first;
+    std::vector<long long> layer_off;
 };
 
 static cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
@@ -190,6 +197,10 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     c->pdf_bytes = pdf_bytes;
     const char* env = std::getenv("LBM_NO_GRAPH");
     c->use_graph = !(env && env[0] == '1');
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        release(c);
+        return fail(LBM_ERR_CUDA, "cudaGetDevice failed");
+    }
 
     c->tgb = p->layout == LBM_LAYOUT_TGB;
     c->ghost_set = T.info.ghost_bytes / 2;
@@ -236,6 +247,21 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     TRY(upload(&c->d_nodes, T.nodes, s));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
+    if (samples.size() == 1) {
+        // tiles are numbered with the slowest axis slowest: each layer is a
+        // contiguous run of tile indices and of PDF values
+        const int n_layers = T.d == 3 ? T.info.ntz : T.info.nty;
+        const int ax = T.d == 3 ? 2 : 1;
+        const long long total = nf > 0 ? T.tile_off[nf - 1] + (long long)c->q * T.tile_stride[nf - 1] : 0;
+        c->layer_first.resize((size_t)n_layers + 1);
+        c->layer_off.resize((size_t)n_layers + 1);
+        int k = 0;
+        for (int l = 0; l <= n_layers; l++) {
+            while (k < nf && T.coords[(size_t)3 * k + ax] < l) k++;
+            c->layer_first[l] = k;
+            c->layer_off[l] = k < nf ? T.tile_off[k] : total;
+        }
+    }
     TRY(upload(&c->d_tile_stride, T.tile_stride, s));
     {
         // one 16-byte load per neighbour slot when the step kernels stage a neighbourhood
@@ -277,10 +303,11 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.f16_inv_scale_f = (float)sa.f16_inv_scale;
     fixed_consts(&c->p, &sa.fx);
     ff_consts(&c->p, &sa.ffc);
-    // LBM_ARITH_AUTO: the FP64 float-float step reads its sources from a
-    // gather table built once here (4 (q + 1) bytes per fluid node), when value
-    // indices fit int32; LBM_ARITH_FF keeps the staged step (no table)
-    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith == LBM_ARITH_AUTO &&
+    // LBM_ARITH_FF_TABLE: the FP64 float-float step reads its sources from a
+    // gather table built once here (4 (q + 1) bytes per fluid node, the
+    // connectivity-matrix scheme of Sec. 2.3.1), when value indices fit int32;
+    // LBM_ARITH_FF / LBM_ARITH_AUTO run the staged tile-map step (no table)
+    if (!c->tgb && p->storage == LBM_STORE_F64 && p->arith == LBM_ARITH_FF_TABLE &&
         !p->persistent && (!p->block_nodes || p->block_nodes == work_threads_for(p->lattice, p->tile_a)) &&
         T.info.pdf_bytes / 8 < (size_t)INT32_MAX && sa.n_nodes > 0) {
         StepLaunch table_step = select_step_ff_table(p->lattice, p->tile_a, p->model);
@@ -616,6 +643,59 @@ extern "C" int lbm_import_pdfs(lbm_ctx* c, const double* pdfs, int64_t step, int
     return publish_ghosts(c, s);
 }
 
+static int check_layers(const lbm_ctx* c, int l_begin, int l_end) {
+    if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+    if (c->layer_first.empty()) return fail(LBM_ERR_ARG, "tile layers need a single-geometry context");
+    if (c->tgb) return fail(LBM_ERR_ARG, "tile layers need the two-copy layout (LBM_LAYOUT_T2C)");
+    const int n = (int)c->layer_first.size() - 1;
+    if (l_begin < 0 || l_end < l_begin || l_end > n)
+        return fail(LBM_ERR_ARG, "tile layers [%d, %d) outside [0, %d)", l_begin, l_end, n);
+    return LBM_OK;
+}
+
+extern "C" int lbm_layer_range(const lbm_ctx* c, int l_begin, int l_end, size_t* offset, size_t* bytes) {
+    int rc = check_layers(c, l_begin, l_end);
+    if (rc) return rc;
+    if (!offset || !bytes) return fail(LBM_ERR_ARG, "NULL argument");
+    const size_t bpv = bytes_per_value(c->p.storage);
+    *offset = (size_t)c->layer_off[l_begin] * bpv;
+    *bytes = (size_t)(c->layer_off[l_end] - c->layer_off[l_begin]) * bpv;
+    return LBM_OK;
+}
+
+extern "C" int lbm_current_copy(const lbm_ctx* c) { return c ? c->cur : -1; }
+
+extern "C" int lbm_moments_layers(lbm_ctx* c, int l_begin, int l_end, lbm_stats* stats, int flags, void* stream) {
+    int rc = check_layers(c, l_begin, l_end);
+    if (rc) return rc;
+    if (!stats) return fail(LBM_ERR_ARG, "stats is NULL");
+    cudaStream_t s = S(stream);
+    const bool residual = flags & LBM_STATS_RESIDUAL;
+    if (residual && !c->d_u_saved)
+        LBM_CUDA_TRY(cudaMalloc(&c->d_u_saved, (size_t)c->na.n_slots * 3 * sizeof(float2) + 8));
+    NodeArgs a = sample_args(c, 0);
+    a.tile_begin = c->layer_first[l_begin];
+    a.n_tiles = c->layer_first[l_end] - c->layer_first[l_begin];
+    a.rho_out = nullptr;
+    a.u_out = nullptr;
+    a.residual = residual ? 1 : 0;
+    a.u_saved = residual ? c->d_u_saved : nullptr;
+    a.partials = c->d_partials;
+    double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (a.n_tiles > 0) {
+        const int nb = node_blocks(c->p.lattice, c->p.tile_a, a.n_tiles);
+        LBM_CUDA_TRY(c->moments_fn(a, s));
+        LBM_CUDA_TRY(launch_reduce(a.partials, nb, c->d_result, s));
+        LBM_CUDA_TRY(cudaMemcpyAsync(r, c->d_result, sizeof(r), cudaMemcpyDeviceToHost, s));
+        LBM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    fill_stats(c, r, residual, c->u_saved_valid, stats);
+    if (residual) c->u_saved_valid = true;
+    if (!finite_stats(*stats))
+        return fail(LBM_ERR_DIVERGED, "mass or momentum is not finite at step %lld", (long long)c->step);
+    return LBM_OK;
+}
+
 extern "C" int lbm_num_samples(const lbm_ctx* c) { return c ? (int)c->samples.size() : 0; }
 
 extern "C" int lbm_get_tiling(const lbm_ctx* c, lbm_tiling* out) {
@@ -634,8 +714,9 @@ extern "C" int lbm_free(lbm_ctx* c) {
 
 namespace lbm {
 // Reduction launch data of a context, for entry points defined in other files.
-int ctx_reduction_args(const lbm_ctx* c, NodeArgs* args, NodeLaunch* moments, int* nblocks) {
+int ctx_reduction_args(const lbm_ctx* c, NodeArgs* args, NodeLaunch* moments, int* nblocks, int* device) {
     if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+    *device = c->device;
     *args = c->na;
     args->pdf = c->pdf[c->cur];
     args->rho_out = nullptr;

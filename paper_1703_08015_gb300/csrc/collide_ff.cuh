@@ -171,6 +171,157 @@ __device__ __noinline__ void update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh
     });
 }
 
+// ---- two float-float numbers at once (f32x2) ------------------------------------
+// sm_100-family GPUs issue two FP32 additions, multiplications or fused
+// multiply-adds in one instruction (add/sub/mul/fma .f32x2).  The collision
+// below evaluates its float-float arithmetic two lanes at a time: two pairs
+// of opposite links, or the two links of one pair.  Every lane performs the
+// operations of the scalar helpers above, in the same order, so the results
+// are the same bits.
+struct ff2 {
+    float2 h, l;
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ ff2 pack2(ff a, ff b) { return ff2{make_float2(a.h, b.h), make_float2(a.l, b.l)}; }
+__device__ __forceinline__ ff lane0(ff2 x) { return ff{x.h.x, x.l.x}; }
+__device__ __forceinline__ ff lane1(ff2 x) { return ff{x.h.y, x.l.y}; }
+__device__ __forceinline__ ff2 ff2_neg(ff2 x) { return ff2{neg2(x.h), neg2(x.l)}; }
+
+__device__ __forceinline__ ff2 fast2_2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return ff2{s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ ff2 two_sum_2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return ff2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ ff2 ff_add_2(ff2 x, ff2 y) {
+    const ff2 s = two_sum_2(x.h, y.h);
+    return fast2_2(s.h, add2(s.l, add2(x.l, y.l)));
+}
+
+__device__ __forceinline__ ff2 ff_add_lazy_2(ff2 x, ff2 y) {
+    const ff2 s = two_sum_2(x.h, y.h);
+    return ff2{s.h, add2(s.l, add2(x.l, y.l))};
+}
+
+__device__ __forceinline__ ff2 ff_mul_2(ff2 x, ff2 y) {
+    const float2 p = mul2(x.h, y.h);
+    float2 e = fma2(x.h, y.h, neg2(p));
+    e = fma2(x.h, y.l, e);
+    e = fma2(x.l, y.h, e);
+    return ff2{p, e};
+}
+
+__device__ __forceinline__ ff2 ff_sqr_2(ff2 x) {
+    const float2 p = mul2(x.h, x.h);
+    float2 e = fma2(x.h, x.h, neg2(p));
+    e = fma2(mul2(bc2(2.f), x.h), x.l, e);
+    return ff2{p, e};
+}
+
+__device__ __forceinline__ ff2 ff_sum3_2(ff2 a, ff2 b, ff2 c) {
+    const ff2 s = two_sum_2(a.h, b.h);
+    const ff2 t = two_sum_2(s.h, c.h);
+    return ff2{t.h, add2(add2(add2(a.l, b.l), add2(c.l, s.l)), t.l)};
+}
+
+__device__ __forceinline__ ff2 ff2_c(const float2 ka, const float2 kb) {
+    return ff2{make_float2(ka.x, kb.x), make_float2(ka.y, kb.y)};
+}
+__device__ __forceinline__ ff2 ff2_bc(const ff k) { return ff2{bc2(k.h), bc2(k.l)}; }
+__device__ __forceinline__ ff2 ff2_k(const FF2C& k) { return ff2{k.h, k.l}; }
+
+// q60_to_ff of two values.
+__device__ __forceinline__ ff2 q60_to_ff_2(long long a, long long b) {
+    const float2 f2 = mul2(make_float2(__int2float_rn((int)(a >> 48)), __int2float_rn((int)(b >> 48))),
+                           bc2(pow2f(-12)));
+    const float2 f1 = mul2(make_float2(__int2float_rn((int)((a >> 24) & 0xFFFFFF)),
+                                       __int2float_rn((int)((b >> 24) & 0xFFFFFF))),
+                           bc2(pow2f(-36)));
+    const float2 f0 = mul2(make_float2(__int2float_rn((int)(a & 0xFFFFFF)), __int2float_rn((int)(b & 0xFFFFFF))),
+                           bc2(pow2f(-60)));
+    const ff2 s = fast2_2(f2, f1);
+    return fast2_2(s.h, add2(s.l, f0));
+}
+
+// d_i (ulps of w_i) of two links as exact float-float pieces (see kept in the
+// scalar form: two 24-bit halves).
+__device__ __forceinline__ ff2 d_to_ff_2(long long a, long long b) {
+    const float2 h = mul2(make_float2(__int2float_rn((int)(a >> 24)), __int2float_rn((int)(b >> 24))),
+                          bc2(pow2f(24)));
+    return ff2{h, make_float2(__int2float_rn((int)(a & 0xFFFFFF)), __int2float_rn((int)(b & 0xFFFFFF)))};
+}
+
+// ulp_round of two results (bit patterns of two links of weight bits wa, wb).
+__device__ __forceinline__ void ulp_round_2(ff2 x, unsigned long long wa, unsigned long long wb, bool& ok,
+                                            unsigned long long& oa, unsigned long long& ob) {
+    ok &= fabsf(x.h.x) < pow2f(47) && fabsf(x.l.x) < pow2f(30) && fabsf(x.h.y) < pow2f(47) &&
+          fabsf(x.l.y) < pow2f(30);
+    const float2 t = mul2(x.h, bc2(pow2f(-24)));
+    const int ha = __float2int_rz(t.x), hb = __float2int_rz(t.y);
+    const float2 rem = fma2(make_float2(__int2float_rn(ha), __int2float_rn(hb)), bc2(-pow2f(24)), x.h);
+    const int la = __float2int_rn(rem.x) + __float2int_rn(x.l.x);
+    const int lb = __float2int_rn(rem.y) + __float2int_rn(x.l.y);
+    oa = wa + (unsigned long long)(((long long)ha << 24) + (long long)la);
+    ob = wb + (unsigned long long)(((long long)hb << 24) + (long long)lb);
+}
+
+// The pair of opposite links that starts at link I (I < opp(I)).
+template <class L, int I>
+struct FFPair {
+    using K = Link<L, I>;
+    static constexpr int i = I, j = K::opp, cls = K::cls;
+    static constexpr int n_comp = (K::cx != 0) + (K::cy != 0) + (K::cz != 0);
+    // k-th nonzero component of c_i: axis (0..2) and sign
+    static constexpr int axis(int k) {
+        int a = 0, n = 0;
+        const int c[3] = {K::cx, K::cy, K::cz};
+        for (a = 0; a < 3; a++)
+            if (c[a] != 0 && n++ == k) return a;
+        return -1;
+    }
+    static constexpr int sign(int k) {
+        const int c[3] = {K::cx, K::cy, K::cz};
+        return c[axis(k)];
+    }
+};
+
+// The first links of the pairs of opposite links, in link order, grouped two
+// by two when both pairs have the same number of nonzero components (and so
+// the same sequence of operations); a pair left alone packs its two links.
+template <class L>
+struct FFGroups;
+template <>
+struct FFGroups<D2Q9> {
+    static constexpr int n = 2;
+    static constexpr int a[2] = {1, 5}, b[2] = {2, 6};
+    static constexpr int lone = -1;
+};
+template <>
+struct FFGroups<D3Q19> {
+    static constexpr int n = 4;
+    static constexpr int a[4] = {1, 7, 11, 15}, b[4] = {3, 9, 13, 17};
+    static constexpr int lone = 5;
+};
+
 template <class L, int MODEL>
 __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], const FixedConsts& k,
                                            const FFConsts& c, unsigned long long* out, int stride) {
@@ -209,8 +360,18 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
     ok &= small_ll(dr, 55) & small_ll(jx, 56) & small_ll(jy, 56) & small_ll(jz, 56);
     if (!ok) return false;
 
-    const ff DR = q60_to_ff(dr), JX = q60_to_ff(jx), JY = q60_to_ff(jy);
-    const ff JZ = L::D == 3 ? q60_to_ff(jz) : ff{0.f, 0.f};
+    const ff2 drjx = q60_to_ff_2(dr, jx);
+    const ff DR = lane0(drjx), JX = lane1(drjx);
+    ff JY, JZ;
+    if constexpr (L::D == 3) {
+        const ff2 t = q60_to_ff_2(jy, jz);
+        JY = lane0(t);
+        JZ = lane1(t);
+    } else {
+        JY = q60_to_ff(jy);
+        JZ = ff{0.f, 0.f};
+    }
+    const ff J[3] = {JX, JY, JZ};
     ff RINV{1.f, 0.f};  // 1 / rho
     if constexpr (MODEL == LBM_QUASI_COMPRESSIBLE) {
         ff rho = fast2(1.f, DR.h);
@@ -224,57 +385,80 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
     }
     // gamma = 1.5 w |p|^2 + 3 (1 - w/2) p.F, p = j + F/2
     // (sums that feed a product are renormalised, the others are lazy)
-    const ff jj = ff_add(ff_add_lazy(ff_sqr(JX), ff_sqr(JY)), ff_sqr(JZ));
-    const ff gamma = ff_add(ff_mul(jj, ff_c(c.g1)),
-                            ff_add_lazy(ff_add_lazy(ff_mul(JX, ff_c(c.kf[0])), ff_mul(JY, ff_c(c.kf[1]))),
-                                        ff_mul(JZ, ff_c(c.kf[2]))));
-    // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V,
-    // formed at the first link of the class (links come class by class)
-    ff V{0.f, 0.f}, C{0.f, 0.f};
-    const ff KEEP = ff_c(c.keep);
-    // (1 - w) g_i in ulps: g_i = d_i ulp(w_i), d_i split into exact 24-bit halves
-    auto kept = [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const ff g{__fmul_rn(__int2float_rn((int)(d[i] >> 24)), pow2f(24)), __int2float_rn((int)(d[i] & 0xFFFFFF))};
-        return ff_mul(g, KEEP);
-    };
-    auto store = [&](auto I, ff x) {
-        constexpr int i = decltype(I)::value;
-        out[i * stride] = ulp_round(x, (unsigned long long)k.w_bits[Link<L, i>::cls], ok);
-    };
-    static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        using K = Link<L, i>;
-        if constexpr (i == ff_first_of_class<L, K::cls>()) {
-            V = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[K::cls])) : ff_c(c.w[K::cls]);
-            C = ff_add_lazy(ff_mul(DR, ff_c(c.rho[K::cls])), ff_neg(ff_mul(gamma, V)));
-        }
-        if constexpr (i == 0) {
-            const ff x = ff_add_lazy(kept(I), C);
-            store(I, x);
-        } else if constexpr (i < K::opp) {
-            constexpr int j = K::opp;
-            constexpr int cl = K::cls;
-            // y = c_i . p
-            ff Y{0.f, 0.f};
-            bool first = true;
-            auto acc = [&](int sgn, const ff& JA) {
-                const ff t = sgn > 0 ? JA : ff_neg(JA);
-                Y = first ? t : ff_add(Y, t);
-                first = false;
-            };
-            if constexpr (K::cx != 0) acc(K::cx, JX);
-            if constexpr (K::cy != 0) acc(K::cy, JY);
-            if constexpr (K::cz != 0) acc(K::cz, JZ);
-            // symmetric part E = C + y (4.5 w y + 9 (1 - w/2) c_i.F) V, antisymmetric part
-            // O = 3 w w_c y + 3 (1 - w/2) w_c c_i.F (all in ulps of w_c)
-            const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[i])));
-            const ff E = ff_add_lazy(C, ff_mul(T, V));
-            const ff O = ff_add_lazy(ff_mul(Y, ff_c(c.j[cl])), ff_c(c.so[i]));
-            store(I, ff_sum3(kept(I), E, O));
-            store(std::integral_constant<int, j>{}, ff_sum3(kept(std::integral_constant<int, j>{}), E, ff_neg(O)));
-        }
+    ff gamma;
+    {
+        const ff2 sq = ff_sqr_2(pack2(JX, JY));
+        const ff2 kfx = ff_mul_2(pack2(JX, JY), ff2_k(c.kf01));
+        const ff jj = ff_add(ff_add_lazy(lane0(sq), lane1(sq)), ff_sqr(JZ));
+        gamma = ff_add(ff_mul(jj, ff_c(c.g1)), ff_add_lazy(ff_add_lazy(lane0(kfx), lane1(kfx)), ff_mul(JZ, ff_c(c.kf[2]))));
+    }
+    // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V
+    ff V[3], C[3];
+    {
+        const ff2 v12 = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul_2(ff2_bc(RINV), ff2_k(c.w12)) : ff2_k(c.w12);
+        const ff2 c12 = ff_add_lazy_2(ff_mul_2(ff2_bc(DR), ff2_k(c.rho12)),
+                                      ff2_neg(ff_mul_2(ff2_bc(gamma), v12)));
+        V[1] = lane0(v12);
+        V[2] = lane1(v12);
+        C[1] = lane0(c12);
+        C[2] = lane1(c12);
+        V[0] = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[0])) : ff_c(c.w[0]);
+        C[0] = ff_add_lazy(ff_mul(DR, ff_c(c.rho[0])), ff_neg(ff_mul(gamma, V[0])));
+    }
+    const ff2 KEEP = ff2_k(c.keep2);
+    const ff2 ALPHA = ff2_k(c.alpha2);
+    // the rest link: (1 - w) g_0 + C_0
+    {
+        const ff g{__fmul_rn(__int2float_rn((int)(d[0] >> 24)), pow2f(24)), __int2float_rn((int)(d[0] & 0xFFFFFF))};
+        const ff x = ff_add_lazy(ff_mul(g, ff_c(c.keep)), C[0]);
+        out[0] = ulp_round(x, (unsigned long long)k.w_bits[0], ok);
+    }
+    // two pairs of opposite links at once: lanes (pair A, pair B)
+    static_for<0, FFGroups<L>::n>([&](auto G) {
+        using PA = FFPair<L, FFGroups<L>::a[decltype(G)::value]>;
+        using PB = FFPair<L, FFGroups<L>::b[decltype(G)::value]>;
+        static_assert(PA::n_comp == PB::n_comp, "grouped pairs take the same operations");
+        // y = c_i . p
+        auto comp = [&](auto Kc) {
+            constexpr int kk = decltype(Kc)::value;
+            const ff a = J[PA::axis(kk)], bb = J[PB::axis(kk)];
+            return pack2(PA::sign(kk) > 0 ? a : ff_neg(a), PB::sign(kk) > 0 ? bb : ff_neg(bb));
+        };
+        ff2 Y = comp(std::integral_constant<int, 0>{});
+        static_for<1, PA::n_comp>([&](auto Kc) { Y = ff_add_2(Y, comp(Kc)); });
+        constexpr int g = decltype(G)::value;
+        const ff2 T = ff_mul_2(Y, ff_add_2(ff_mul_2(Y, ALPHA), ff2_k(c.beta2[g])));
+        const ff2 VV = pack2(V[PA::cls], V[PB::cls]);
+        const ff2 E = ff_add_lazy_2(pack2(C[PA::cls], C[PB::cls]), ff_mul_2(T, VV));
+        const ff2 O = ff_add_lazy_2(ff_mul_2(Y, ff2_k(c.j2[g])), ff2_k(c.so2[g]));
+        const ff2 xi = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::i], d[PB::i]), KEEP), E, O);
+        const ff2 xj = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::j], d[PB::j]), KEEP), E, ff2_neg(O));
+        unsigned long long r0, r1;
+        ulp_round_2(xi, (unsigned long long)k.w_bits[PA::cls], (unsigned long long)k.w_bits[PB::cls], ok, r0, r1);
+        out[PA::i * stride] = r0;
+        out[PB::i * stride] = r1;
+        ulp_round_2(xj, (unsigned long long)k.w_bits[PA::cls], (unsigned long long)k.w_bits[PB::cls], ok, r0, r1);
+        out[PA::j * stride] = r0;
+        out[PB::j * stride] = r1;
     });
+    // a pair left alone: lanes (link i, link opp(i))
+    if constexpr (FFGroups<L>::lone > 0) {
+        using P = FFPair<L, FFGroups<L>::lone>;
+        ff Y{0.f, 0.f};
+        static_for<0, P::n_comp>([&](auto Kc) {
+            constexpr int kk = decltype(Kc)::value;
+            const ff t = P::sign(kk) > 0 ? J[P::axis(kk)] : ff_neg(J[P::axis(kk)]);
+            Y = kk == 0 ? t : ff_add(Y, t);
+        });
+        const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[P::i])));
+        const ff E = ff_add_lazy(C[P::cls], ff_mul(T, V[P::cls]));
+        const ff O = ff_add_lazy(ff_mul(Y, ff_c(c.j[P::cls])), ff_c(c.so[P::i]));
+        const ff2 x = ff_sum3_2(ff_mul_2(d_to_ff_2(d[P::i], d[P::j]), KEEP), ff2_bc(E), pack2(O, ff_neg(O)));
+        unsigned long long r0, r1;
+        ulp_round_2(x, (unsigned long long)k.w_bits[P::cls], (unsigned long long)k.w_bits[P::cls], ok, r0, r1);
+        out[P::i * stride] = r0;
+        out[P::j * stride] = r1;
+    }
     return ok;
 }
 

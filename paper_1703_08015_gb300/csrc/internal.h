@@ -77,6 +77,12 @@ struct FixedConsts {
     long long dws;        // sum_i w_i in Q60, minus 2^60 (exact)
 };
 
+// Two float-float constants laid out for the f32x2 instructions: the high
+// parts of lanes 0 and 1, then their low parts.
+struct FF2C {
+    float2 h, l;
+};
+
 // Constants of the float-float FP64 path: each a (hi, lo) pair of floats.
 struct FFConsts {      // u_c = 1 / ulp(w_c): class quantities in ulps of w_c
     float2 w[3];       // w_c u_c
@@ -88,6 +94,11 @@ struct FFConsts {      // u_c = 1 / ulp(w_c): class quantities in ulps of w_c
     float2 kf[3];      // 3 (1 - w/2) F_a
     float2 beta[19];   // 9 (1 - w/2) (c_i.F)
     float2 so[19];     // 3 (1 - w/2) w_i (c_i.F) u_c
+    // the same, two lanes at a time: (x, x) for keep and alpha, classes (1, 2)
+    // for w and rho, (kf_x, kf_y), and per group of two pairs of opposite
+    // links (first links a_g, b_g) beta, j of their classes and so
+    FF2C keep2, alpha2, w12, rho12, kf01;
+    FF2C beta2[4], j2[4], so2[4];
 };
 
 // Constants of the FP32 collision (reduced storage forms), per weight class c

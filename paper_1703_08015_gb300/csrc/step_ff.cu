@@ -170,6 +170,8 @@ static float2 split(double v) {
     return make_float2(h, (float)(v - (double)h));
 }
 
+static FF2C lanes(float2 a, float2 b) { return FF2C{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
+
 template <class L>
 static void ff_consts_for(const lbm_params* p, FFConsts* k) {
     const double omega = 1.0 / p->tau;
@@ -196,6 +198,17 @@ static void ff_consts_for(const lbm_params* p, FFConsts* k) {
         const double cF = L::cx_[i] * F[0] + L::cy_[i] * F[1] + L::cz_[i] * F[2];
         k->beta[i] = split(9.0 * kf * cF);
         k->so[i] = split(3.0 * kf * L::wc_[L::cls_[i]] * cF * to_ulp[L::cls_[i]]);
+    }
+    k->keep2 = lanes(k->keep, k->keep);
+    k->alpha2 = lanes(k->alpha, k->alpha);
+    k->w12 = lanes(k->w[1], k->w[2]);
+    k->rho12 = lanes(k->rho[1], k->rho[2]);
+    k->kf01 = lanes(k->kf[0], k->kf[1]);
+    for (int g = 0; g < FFGroups<L>::n; g++) {
+        const int a = FFGroups<L>::a[g], b = FFGroups<L>::b[g];
+        k->beta2[g] = lanes(k->beta[a], k->beta[b]);
+        k->j2[g] = lanes(k->j[L::cls_[a]], k->j[L::cls_[b]]);
+        k->so2[g] = lanes(k->so[a], k->so[b]);
     }
 }
 

@@ -257,7 +257,8 @@ template <class L, int A, int MODEL>
 static StepLaunch pick_tgb(int storage, int arith) {
     if (storage == LBM_STORE_F64) {
         if (arith == LBM_ARITH_F64) return &launch_step_tgb<L, A, MODEL, StoreF64, 2>;
-        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO) return &launch_step_tgb<L, A, MODEL, StoreF64, 1>;
+        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO || arith == LBM_ARITH_FF_TABLE)
+            return &launch_step_tgb<L, A, MODEL, StoreF64, 1>;
         return nullptr;
     }
     if (storage == LBM_STORE_F32) return &launch_step_tgb<L, A, MODEL, StoreF32, 0>;

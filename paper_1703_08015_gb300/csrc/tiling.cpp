@@ -92,6 +92,8 @@ int validate_params(const lbm_params* p) {
     if (!bytes_per_value(p->storage)) return fail(LBM_ERR_ARG, "unknown storage %d", p->storage);
     if (p->model != LBM_QUASI_COMPRESSIBLE && p->model != LBM_INCOMPRESSIBLE)
         return fail(LBM_ERR_ARG, "unknown model %d", p->model);
+    if (p->arith < LBM_ARITH_AUTO || p->arith > LBM_ARITH_FF_TABLE)
+        return fail(LBM_ERR_ARG, "unknown arithmetic %d", p->arith);
     const int d = p->lattice == LBM_D2Q9 ? 2 : 3;
     const int n[3] = {p->nx, p->ny, p->nz};
     for (int ax = 0; ax < d; ax++)

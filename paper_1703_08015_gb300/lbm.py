@@ -21,14 +21,15 @@ ERRORS = {-1: "LBM_ERR_ARG", -2: "LBM_ERR_SHAPE", -3: "LBM_ERR_CUDA", -4: "LBM_E
 LBM_D2Q9, LBM_D3Q19 = 9, 19
 LBM_QUASI_COMPRESSIBLE, LBM_INCOMPRESSIBLE = 0, 1
 LBM_STORE_F64, LBM_STORE_F32, LBM_STORE_F16S, LBM_STORE_F32S = 0, 1, 2, 3
-LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED, LBM_ARITH_FF = 0, 1, 2, 3
+LBM_ARITH_AUTO, LBM_ARITH_F64, LBM_ARITH_FIXED, LBM_ARITH_FF, LBM_ARITH_FF_TABLE = 0, 1, 2, 3, 4
 LBM_OUT_DEVICE, LBM_STATS_RESIDUAL = 1, 2
 LBM_LAYOUT_T2C, LBM_LAYOUT_TGB = 0, 1
 
 EXPORTED = ("lbm_build_tilemap", "lbm_init", "lbm_step", "lbm_moments", "lbm_export_pdfs",
             "lbm_import_pdfs", "lbm_get_tiling", "lbm_free", "lbm_last_error", "lbm_stats_noalloc",
             "lbm_build_tilemap_batch", "lbm_init_batch", "lbm_moments_batch", "lbm_export_pdfs_sample",
-            "lbm_num_samples", "lbm_moments_sample", "lbm_filter_period2")
+            "lbm_num_samples", "lbm_moments_sample", "lbm_filter_period2", "lbm_layer_range",
+            "lbm_current_copy", "lbm_moments_layers")
 LBM_NOALLOC_MAX_BLOCKS = 8192
 
 
@@ -92,6 +93,9 @@ def library(build: bool = True):
             lib.lbm_num_samples.argtypes = [P]
             lib.lbm_moments_sample.argtypes = [P, I, P, P, I, P]
             lib.lbm_filter_period2.argtypes = [P, P]
+            lib.lbm_layer_range.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+            lib.lbm_current_copy.argtypes = [P]
+            lib.lbm_moments_layers.argtypes = [P, I, I, ctypes.POINTER(lbm_stats), I, P]
             lib.lbm_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
                 getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int

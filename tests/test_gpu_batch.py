@@ -93,3 +93,43 @@ def test_batch_global_stats_are_the_sum_of_samples():
         b.close()
     assert st.n_fluid == sum(p.n_fluid for p in per)
     assert st.mass == pytest.approx(sum(p.mass for p in per), rel=1e-15)
+
+
+def test_autotune_picks_a_compiled_mapping_and_reuses_its_cache(tmp_path, monkeypatch):
+    """The tuner times every compiled candidate for the batch, returns the
+    fastest, caches it under the GPU / lattice / storage / workload key, and
+    a second call reads the cache without timing anything; the chosen
+    mapping computes the same bits as the default one."""
+    _cuda()
+    from paper_1703_08015_gb300 import autotune
+
+    masks = _samples()
+    storage = lbm.LBM_STORE_F32S
+    cache = tmp_path / "autotune.json"
+    cands = autotune.candidates(19, storage, masks, ARGS["periodic"])
+    assert {"tile_a": 4, "block_nodes": 0, "persistent": 0} in cands
+    best, trials = autotune.tune(masks, 19, storage, steps=8, cache_path=str(cache), **ARGS)
+    assert best in cands
+    assert len(trials) == len(cands) and all(v > 0 for v in trials.values())
+    assert trials[f"a{best['tile_a']}_b{best['block_nodes']}_p{best['persistent']}"] == max(trials.values())
+    assert cache.exists()
+
+    def no_timing(*a, **k):
+        raise AssertionError("a cached choice was timed again")
+
+    monkeypatch.setattr(autotune, "time_mapping", no_timing)
+    again, trials2 = autotune.tune(masks, 19, storage, steps=8, cache_path=str(cache), **ARGS)
+    assert again == best and trials2 == trials
+
+    res = []
+    for cfg in ({"tile_a": 4, "block_nodes": 0, "persistent": 0}, best):
+        b = lbm.BatchSolver(masks, 19, cfg["tile_a"], storage=storage, block_nodes=cfg["block_nodes"],
+                            persistent=cfg["persistent"], **ARGS)
+        try:
+            b.step(40)
+            res.append([b.export_pdfs(k) for k in range(len(masks))])
+        finally:
+            b.close()
+    for a, c, m in zip(res[0], res[1], masks):
+        fl = m.astype(bool)
+        assert np.array_equal(a[:, fl].view(np.uint64), c[:, fl].view(np.uint64))
