@@ -75,11 +75,14 @@ int lbm_nn_weight_flip(const void* wgt, int cin, int cout, void* wt, void* strea
 
 /* dw[tap][ci][co] += sum_p x[p + off(tap)][ci] * dy[p][co] (off and `wrap`
  * as in lbm_nn_conv3d) and, when dbias is not NULL, dbias[co] += sum_p
- * dy[p][co] (FP32 accumulators; the sums over voxel chunks are added
- * atomically, so the last bits depend on their order).  For 8 <= cin <= 256
+ * dy[p][co] (FP32 accumulators).  The voxels are split into chunks whose
+ * partial sums are stored, then added to dw / dbias in chunk order: the
+ * result is the same bits on every call (no atomics).  For 8 <= cin <= 256
  * the sums run on the tcgen05 tensor cores as one GEMM per tap over operands
- * packed channel-major into a library-owned device buffer (grown on demand,
- * kept for the process; calls must not overlap on different streams). */
+ * packed channel-major; the packed operands and the partial sums live in
+ * library-owned device buffers (grown on demand, kept for the process; calls
+ * must not overlap on different streams).  Errors: LBM_ERR_ARG, LBM_ERR_OOM
+ * (no room for the partial sums), LBM_ERR_CUDA. */
 int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout,
                         int wrap, float* dw, float* dbias, void* stream);
 

@@ -243,10 +243,18 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     TRY(upload(&c->d_nbr, T.nbr, s));
     TRY(upload(&c->d_tmask, T.tmask, s));
     TRY(upload(&c->d_coords, T.coords, s));
-    build_work_list(&T, p->block_nodes ? p->block_nodes : work_threads_for(p->lattice, p->tile_a), 16);
-    TRY(upload(&c->d_nodes, T.nodes, s));
+    // work blocks on the host; the fluid-node list they index is written on
+    // the device from the tile masks (20 MB for 5 M fluid nodes not copied)
+    const long long n_nodes =
+        build_work_list(&T, p->block_nodes ? p->block_nodes : work_threads_for(p->lattice, p->tile_a), 16, false);
+    CTRY(cudaMalloc(&c->d_nodes, (size_t)std::max<long long>(n_nodes, 1) * sizeof(uint32_t)));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
+    {
+        NodeListLaunch nl = select_node_list(p->lattice, p->tile_a);
+        if (!nl) TRY(fail(LBM_ERR_ARG, "no node-list kernel for lattice %d, tile %d", p->lattice, p->tile_a));
+        CTRY(nl(c->d_tmask, c->d_tile_off, nf, c->d_nodes, s));
+    }
     if (samples.size() == 1) {
         // tiles are numbered with the slowest axis slowest: each layer is a
         // contiguous run of tile indices and of PDF values
@@ -290,7 +298,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.tile_stride = c->d_tile_stride;
     sa.tinfo = c->d_tinfo;
     sa.n_tiles = nf;
-    sa.n_nodes = (long long)T.nodes.size();
+    sa.n_nodes = n_nodes;
     sa.tau = p->tau;
     sa.omega = 1.0 / p->tau;
     for (int k = 0; k < 3; k++) sa.force[k] = (k < 2 || p->lattice == LBM_D3Q19) ? p->force[k] : 0.0;

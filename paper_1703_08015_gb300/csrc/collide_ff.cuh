@@ -128,21 +128,30 @@ __device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
     return ff{t.h, __fadd_rn(__fadd_rn(__fadd_rn(a.l, b.l), __fadd_rn(c.l, s.l)), t.l)};
 }
 
-// FP64 bit pattern of w + r ulp(w) with r the integer within one unit of
-// x = x.h + x.l (units of ulp(w)): x.h splits exactly into hi 2^24 + rem, and
-// rem and x.l are rounded to integers separately.  (A single FP32 -> int64
-// conversion of x.h is slower here: those conversions issue at a fraction of
-// the 32-bit rate.)
+// FP64 bit pattern of w + r ulp(w) with r = RN(x.h) + RN(x.l), within one unit
+// of x = x.h + x.l (units of ulp(w)).  x.h is split at 2^24 by rounding it to
+// the nearest multiple of 2^24 with one addition: t = x.h + 1.5 2^47 lies in
+// [2^47, 2^48) for |x.h| < 2^46, where the floats are the multiples of 2^24, so
+// bits(t) - bits(1.5 2^47) counts them and the remainder x.h - (t - 1.5 2^47)
+// is exact (|rem| <= 2^23).  Subtracting an even integer commutes with
+// round-to-nearest-even, so RN(rem) + (t - 1.5 2^47) = RN(x.h).  (Three FP32
+// <-> int conversions per value, as a truncating split would take, issue at
+// a fraction of the FP32 rate.)
 //
 // The result stays in the binade of w (same sign and exponent bits): |r| <
-// 2^47 + 2^30 + 1 ulps, and every lattice weight lies at least 2^48 ulps from
+// 2^46 + 2^30 + 1 ulps, and every lattice weight lies at least 2^48 ulps from
 // the edges of its binade (checked at compile time in collide_ff).
+constexpr float kSplit24 = 211106232532992.0f;  // 1.5 * 2^47: floats in [2^47, 2^48) are multiples of 2^24
+__device__ __forceinline__ unsigned long long ulp_assemble(unsigned long long wb, float t, int lo) {
+    const long long k = (long long)wb - ((long long)__float_as_int(kSplit24) << 24);
+    return (unsigned long long)(k + ((long long)(unsigned)__float_as_int(t) << 24) + (long long)lo);
+}
+
 __device__ __forceinline__ unsigned long long ulp_round(ff x, unsigned long long wb, bool& ok) {
-    ok &= fabsf(x.h) < pow2f(47) && fabsf(x.l) < pow2f(30);
-    const int hi = __float2int_rz(__fmul_rn(x.h, pow2f(-24)));            // |hi| < 2^23
-    const float rem = __fmaf_rn(__int2float_rn(hi), -pow2f(24), x.h);     // exact, |rem| < 2^24
-    const int lo = __float2int_rn(rem) + __float2int_rn(x.l);
-    return wb + (unsigned long long)(((long long)hi << 24) + (long long)lo);
+    ok &= fabsf(x.h) < pow2f(46) && fabsf(x.l) < pow2f(30);
+    const float t = __fadd_rn(x.h, kSplit24);
+    const float rem = __fsub_rn(x.h, __fsub_rn(t, kSplit24));  // exact, |rem| <= 2^23
+    return ulp_assemble(wb, t, __float2int_rn(rem) + __float2int_rn(x.l));
 }
 
 template <class L, int C>
@@ -273,15 +282,12 @@ __device__ __forceinline__ ff2 d_to_ff_2(long long a, long long b) {
 // ulp_round of two results (bit patterns of two links of weight bits wa, wb).
 __device__ __forceinline__ void ulp_round_2(ff2 x, unsigned long long wa, unsigned long long wb, bool& ok,
                                             unsigned long long& oa, unsigned long long& ob) {
-    ok &= fabsf(x.h.x) < pow2f(47) && fabsf(x.l.x) < pow2f(30) && fabsf(x.h.y) < pow2f(47) &&
+    ok &= fabsf(x.h.x) < pow2f(46) && fabsf(x.l.x) < pow2f(30) && fabsf(x.h.y) < pow2f(46) &&
           fabsf(x.l.y) < pow2f(30);
-    const float2 t = mul2(x.h, bc2(pow2f(-24)));
-    const int ha = __float2int_rz(t.x), hb = __float2int_rz(t.y);
-    const float2 rem = fma2(make_float2(__int2float_rn(ha), __int2float_rn(hb)), bc2(-pow2f(24)), x.h);
-    const int la = __float2int_rn(rem.x) + __float2int_rn(x.l.x);
-    const int lb = __float2int_rn(rem.y) + __float2int_rn(x.l.y);
-    oa = wa + (unsigned long long)(((long long)ha << 24) + (long long)la);
-    ob = wb + (unsigned long long)(((long long)hb << 24) + (long long)lb);
+    const float2 t = add2(x.h, bc2(kSplit24));
+    const float2 rem = sub2(x.h, sub2(t, bc2(kSplit24)));  // exact, |rem| <= 2^23
+    oa = ulp_assemble(wa, t.x, __float2int_rn(rem.x) + __float2int_rn(x.l.x));
+    ob = ulp_assemble(wb, t.y, __float2int_rn(rem.y) + __float2int_rn(x.l.y));
 }
 
 // The pair of opposite links that starts at link I (I < opp(I)).
@@ -337,19 +343,23 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         d[i] = (long long)(b[i] - (unsigned long long)k.w_bits[Link<L, i>::cls]);
         ok &= within_2p47(d[i]);  // also rejects another binade, sign, NaN/Inf
     });
-    // exact sums per class (units of ulp(w_c)), then one shift per class to 2^-60
-    long long sr[3] = {0, 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
-    static_for<0, Q>([&](auto I) {
+    // exact sums per class (units of ulp(w_c)), then one shift per class to
+    // 2^-60; each pair of opposite links enters through its sum and difference
+    long long sr[3] = {d[0], 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
+    static_for<1, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         using K = Link<L, i>;
-        constexpr int cl = K::cls;
-        sr[cl] += d[i];
-        if constexpr (K::cx > 0) sx[cl] += d[i];
-        if constexpr (K::cx < 0) sx[cl] -= d[i];
-        if constexpr (K::cy > 0) sy[cl] += d[i];
-        if constexpr (K::cy < 0) sy[cl] -= d[i];
-        if constexpr (K::cz > 0) sz[cl] += d[i];
-        if constexpr (K::cz < 0) sz[cl] -= d[i];
+        if constexpr (i < K::opp) {
+            constexpr int cl = K::cls;
+            const long long sp = d[i] + d[K::opp], dp = d[i] - d[K::opp];
+            sr[cl] += sp;
+            if constexpr (K::cx > 0) sx[cl] += dp;
+            if constexpr (K::cx < 0) sx[cl] -= dp;
+            if constexpr (K::cy > 0) sy[cl] += dp;
+            if constexpr (K::cy < 0) sy[cl] -= dp;
+            if constexpr (K::cz > 0) sz[cl] += dp;
+            if constexpr (K::cz < 0) sz[cl] -= dp;
+        }
     });
     constexpr int S0 = FFLink<L, ff_first_of_class<L, 0>()>::SHIFT, S1 = FFLink<L, ff_first_of_class<L, 1>()>::SHIFT,
                   S2 = FFLink<L, ff_first_of_class<L, 2>()>::SHIFT;
@@ -360,15 +370,16 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
     ok &= small_ll(dr, 55) & small_ll(jx, 56) & small_ll(jy, 56) & small_ll(jz, 56);
     if (!ok) return false;
 
-    const ff2 drjx = q60_to_ff_2(dr, jx);
-    const ff DR = lane0(drjx), JX = lane1(drjx);
-    ff JY, JZ;
+    // (j_x, j_y) side by side: the first group's c_i . p of its two pairs
+    const ff2 JXY = q60_to_ff_2(jx, jy);
+    const ff JX = lane0(JXY), JY = lane1(JXY);
+    ff DR, JZ;
     if constexpr (L::D == 3) {
-        const ff2 t = q60_to_ff_2(jy, jz);
-        JY = lane0(t);
+        const ff2 t = q60_to_ff_2(dr, jz);
+        DR = lane0(t);
         JZ = lane1(t);
     } else {
-        JY = q60_to_ff(jy);
+        DR = q60_to_ff(dr);
         JZ = ff{0.f, 0.f};
     }
     const ff J[3] = {JX, JY, JZ};
@@ -387,37 +398,35 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
     // (sums that feed a product are renormalised, the others are lazy)
     ff gamma;
     {
-        const ff2 sq = ff_sqr_2(pack2(JX, JY));
-        const ff2 kfx = ff_mul_2(pack2(JX, JY), ff2_k(c.kf01));
+        const ff2 sq = ff_sqr_2(JXY);
+        const ff2 kfx = ff_mul_2(JXY, ff2_k(c.kf01));
         const ff jj = ff_add(ff_add_lazy(lane0(sq), lane1(sq)), ff_sqr(JZ));
         gamma = ff_add(ff_mul(jj, ff_c(c.g1)), ff_add_lazy(ff_add_lazy(lane0(kfx), lane1(kfx)), ff_mul(JZ, ff_c(c.kf[2]))));
     }
-    // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V
-    ff V[3], C[3];
-    {
-        const ff2 v12 = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul_2(ff2_bc(RINV), ff2_k(c.w12)) : ff2_k(c.w12);
-        const ff2 c12 = ff_add_lazy_2(ff_mul_2(ff2_bc(DR), ff2_k(c.rho12)),
-                                      ff2_neg(ff_mul_2(ff2_bc(gamma), v12)));
-        V[1] = lane0(v12);
-        V[2] = lane1(v12);
-        C[1] = lane0(c12);
-        C[2] = lane1(c12);
-        V[0] = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[0])) : ff_c(c.w[0]);
-        C[0] = ff_add_lazy(ff_mul(DR, ff_c(c.rho[0])), ff_neg(ff_mul(gamma, V[0])));
-    }
+    // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V;
+    // classes 1 and 2 in both lanes (each group of pairs is single-class), each
+    // formed right before the links of its class
     const ff2 KEEP = ff2_k(c.keep2);
     const ff2 ALPHA = ff2_k(c.alpha2);
     // the rest link: (1 - w) g_0 + C_0
     {
+        const ff V0 = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul(RINV, ff_c(c.w[0])) : ff_c(c.w[0]);
+        const ff C0 = ff_add_lazy(ff_mul(DR, ff_c(c.rho[0])), ff_neg(ff_mul(gamma, V0)));
         const ff g{__fmul_rn(__int2float_rn((int)(d[0] >> 24)), pow2f(24)), __int2float_rn((int)(d[0] & 0xFFFFFF))};
-        const ff x = ff_add_lazy(ff_mul(g, ff_c(c.keep)), C[0]);
+        const ff x = ff_add_lazy(ff_mul(g, ff_c(c.keep)), C0);
         out[0] = ulp_round(x, (unsigned long long)k.w_bits[0], ok);
     }
+    auto class_consts = [&](const FF2C& wcc, const FF2C& rcc, ff2& VV, ff2& CC) {
+        VV = MODEL == LBM_QUASI_COMPRESSIBLE ? ff_mul_2(ff2_bc(RINV), ff2_k(wcc)) : ff2_k(wcc);
+        CC = ff_add_lazy_2(ff_mul_2(ff2_bc(DR), ff2_k(rcc)), ff2_neg(ff_mul_2(ff2_bc(gamma), VV)));
+    };
     // two pairs of opposite links at once: lanes (pair A, pair B)
-    static_for<0, FFGroups<L>::n>([&](auto G) {
-        using PA = FFPair<L, FFGroups<L>::a[decltype(G)::value]>;
-        using PB = FFPair<L, FFGroups<L>::b[decltype(G)::value]>;
+    auto group = [&](auto G, const ff2& VV, const ff2& CC) {
+        constexpr int g = decltype(G)::value;
+        using PA = FFPair<L, FFGroups<L>::a[g]>;
+        using PB = FFPair<L, FFGroups<L>::b[g]>;
         static_assert(PA::n_comp == PB::n_comp, "grouped pairs take the same operations");
+        static_assert(PA::cls == PB::cls && PA::cls > 0, "a group takes one class of links");
         // y = c_i . p
         auto comp = [&](auto Kc) {
             constexpr int kk = decltype(Kc)::value;
@@ -426,24 +435,22 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         };
         ff2 Y = comp(std::integral_constant<int, 0>{});
         static_for<1, PA::n_comp>([&](auto Kc) { Y = ff_add_2(Y, comp(Kc)); });
-        constexpr int g = decltype(G)::value;
         const ff2 T = ff_mul_2(Y, ff_add_2(ff_mul_2(Y, ALPHA), ff2_k(c.beta2[g])));
-        const ff2 VV = pack2(V[PA::cls], V[PB::cls]);
-        const ff2 E = ff_add_lazy_2(pack2(C[PA::cls], C[PB::cls]), ff_mul_2(T, VV));
+        const ff2 E = ff_add_lazy_2(CC, ff_mul_2(T, VV));
         const ff2 O = ff_add_lazy_2(ff_mul_2(Y, ff2_k(c.j2[g])), ff2_k(c.so2[g]));
         const ff2 xi = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::i], d[PB::i]), KEEP), E, O);
-        const ff2 xj = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::j], d[PB::j]), KEEP), E, ff2_neg(O));
         unsigned long long r0, r1;
         ulp_round_2(xi, (unsigned long long)k.w_bits[PA::cls], (unsigned long long)k.w_bits[PB::cls], ok, r0, r1);
         out[PA::i * stride] = r0;
         out[PB::i * stride] = r1;
+        const ff2 xj = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::j], d[PB::j]), KEEP), E, ff2_neg(O));
         ulp_round_2(xj, (unsigned long long)k.w_bits[PA::cls], (unsigned long long)k.w_bits[PB::cls], ok, r0, r1);
         out[PA::j * stride] = r0;
         out[PB::j * stride] = r1;
-    });
+    };
     // a pair left alone: lanes (link i, link opp(i))
-    if constexpr (FFGroups<L>::lone > 0) {
-        using P = FFPair<L, FFGroups<L>::lone>;
+    auto lone = [&](auto LN, const ff2& VV, const ff2& CC) {
+        using P = FFPair<L, decltype(LN)::value>;
         ff Y{0.f, 0.f};
         static_for<0, P::n_comp>([&](auto Kc) {
             constexpr int kk = decltype(Kc)::value;
@@ -451,13 +458,26 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
             Y = kk == 0 ? t : ff_add(Y, t);
         });
         const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[P::i])));
-        const ff E = ff_add_lazy(C[P::cls], ff_mul(T, V[P::cls]));
+        const ff E = ff_add_lazy(lane0(CC), ff_mul(T, lane0(VV)));
         const ff O = ff_add_lazy(ff_mul(Y, ff_c(c.j[P::cls])), ff_c(c.so[P::i]));
         const ff2 x = ff_sum3_2(ff_mul_2(d_to_ff_2(d[P::i], d[P::j]), KEEP), ff2_bc(E), pack2(O, ff_neg(O)));
         unsigned long long r0, r1;
         ulp_round_2(x, (unsigned long long)k.w_bits[P::cls], (unsigned long long)k.w_bits[P::cls], ok, r0, r1);
         out[P::i * stride] = r0;
         out[P::j * stride] = r1;
+    };
+    static_assert(FFGroups<L>::lone < 0 || Link<L, (FFGroups<L>::lone > 0 ? FFGroups<L>::lone : 1)>::cls == 1,
+                  "the lone pair is of class 1");
+    {  // class 1: the first group and the lone pair
+        ff2 VV, CC;
+        class_consts(c.w11, c.rho11, VV, CC);
+        group(std::integral_constant<int, 0>{}, VV, CC);
+        if constexpr (FFGroups<L>::lone > 0) lone(std::integral_constant<int, FFGroups<L>::lone>{}, VV, CC);
+    }
+    {  // class 2: the other groups
+        ff2 VV, CC;
+        class_consts(c.w22, c.rho22, VV, CC);
+        static_for<1, FFGroups<L>::n>([&](auto G) { group(G, VV, CC); });
     }
     return ok;
 }

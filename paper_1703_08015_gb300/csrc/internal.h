@@ -51,9 +51,10 @@ int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_
                        std::vector<SampleRange>* samples);
 int validate_params(const lbm_params* p);
 int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out);
-// Fluid-node list and step-kernel blocks of at most `threads` nodes and
-// `max_tiles` tiles each.
-void build_work_list(HostTiling* T, int threads, int max_tiles);
+// Step-kernel blocks of at most `threads` nodes and `max_tiles` tiles each,
+// and (want_nodes) the fluid-node list on the host; returns the number of
+// fluid nodes (entries of the list).
+long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes = true);
 int work_threads_for(int lattice, int a);
 int lattice_q(int lattice);
 size_t bytes_per_value(int storage);
@@ -98,6 +99,7 @@ struct FFConsts {      // u_c = 1 / ulp(w_c): class quantities in ulps of w_c
     // for w and rho, (kf_x, kf_y), and per group of two pairs of opposite
     // links (first links a_g, b_g) beta, j of their classes and so
     FF2C keep2, alpha2, w12, rho12, kf01;
+    FF2C w11, w22, rho11, rho22;  // (w_c, w_c) and (w w_c, w w_c) of classes 1 and 2
     FF2C beta2[4], j2[4], so2[4];
 };
 
@@ -168,6 +170,11 @@ struct NodeArgs {         // kernels that visit every node of every tile
 };
 
 using StepLaunch = cudaError_t (*)(const StepArgs&, cudaStream_t);
+// The fluid-node list of build_work_list written on the device from the tile
+// masks and compact offsets (nullptr when a geometry is not compiled).
+using NodeListLaunch = cudaError_t (*)(const uint64_t* tmask, const long long* tile_off, int n_tiles,
+                                       uint32_t* nodes, cudaStream_t);
+NodeListLaunch select_node_list(int lattice, int a);
 using NodeLaunch = cudaError_t (*)(const NodeArgs&, cudaStream_t);
 
 // Kernel selection (nullptr when a combination is not compiled).

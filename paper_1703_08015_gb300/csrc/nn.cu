@@ -147,11 +147,12 @@ __global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ x, int N,
             }
 }
 
-// dW[(tap,ci)][co] += sum_p x[p + off(tap)][ci] dy[p][co]: GEMM with 64 rows of
+// dW[(tap,ci)][co] = sum_p x[p + off(tap)][ci] dy[p][co]: GEMM with 64 rows of
 // (tap, ci) per block, NF*8 output channels from blockIdx.z * NF*8, split over
-// voxel chunks (blockIdx.y) whose partial sums are added atomically.  The
-// gather form, for the shapes the tcgen05 weight gradient does not take
-// (fewer than 8 input channels, more than 256).
+// voxel chunks (blockIdx.y); each block stores its chunk's partial sums to
+// part[blockIdx.y], added to dw in chunk order afterwards.  The gather form,
+// for the shapes the tcgen05 weight gradient does not take (fewer than 8
+// input channels, more than 256).
 template <int NF>
 __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int N,
                                                int D, int H, int W, int Cin, int Cout, int wrap,
@@ -234,18 +235,19 @@ __global__ void __launch_bounds__(128) k_wgrad(const bf16* __restrict__ x, const
             for (int j = 0; j < 2; j++) {
                 const int row = k0 + warp * 16 + (lane >> 2) + h2 * 8;
                 const int co = n0 + f * 8 + (lane & 3) * 2 + j;
-                if (row < K && co < Cout) atomicAdd(&dw[(long long)row * Cout + co], acc[f][h2 * 2 + j]);
+                if (row < K && co < Cout) dw[(long long)blockIdx.y * K * Cout + (long long)row * Cout + co] = acc[f][h2 * 2 + j];
             }
 }
 
-__global__ void k_bias_grad(const bf16* __restrict__ dy, long long M, int C, float* __restrict__ db,
+// Partial bias gradients of row blocks: part[blockIdx.x][c] = sum of dy over the block's rows.
+__global__ void k_bias_grad(const bf16* __restrict__ dy, long long M, int C, float* __restrict__ part,
                             long long rows_per_block) {
     const long long r0 = (long long)blockIdx.x * rows_per_block;
     const long long r1 = r0 + rows_per_block < M ? r0 + rows_per_block : M;
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         float s = 0.f;
         for (long long r = r0; r < r1; r++) s += __bfloat162float(dy[r * C + c]);
-        atomicAdd(&db[c], s);
+        part[(long long)blockIdx.x * C + c] = s;
     }
 }
 
@@ -471,6 +473,8 @@ namespace lbm {
 namespace nn {
 int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* wgt, const float* bias, int cout,
                 int relu, int wrap, void* y, float* y32, cudaStream_t s);
+float* chunk_scratch(size_t floats);
+int sum_chunks(const float* part, long long chunks, long long E, float* dst, cudaStream_t s);
 int wgrad_tc(const void* x, const void* dy, int n, int d, int h, int w, int cin, int cout, int wrap, float* dw,
              cudaStream_t s);
 }  // namespace nn
@@ -523,40 +527,41 @@ extern "C" int lbm_nn_conv3d_wgrad(const void* x, const void* dy, int n, int d, 
     if (!x || !dy || !dw || n < 1 || d < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (wrap & ~7))
         return fail(LBM_ERR_ARG, "lbm_nn_conv3d_wgrad: bad arguments");
     // the tcgen05 GEMMs over packed operands where the shape allows, else the
-    // gather kernel below
+    // gather kernel below; both leave per-chunk partial sums that are added in
+    // chunk order (the result does not depend on the order blocks finish in)
     int rc = wgrad_tc(x, dy, n, d, h, w, cin, cout, wrap, dw, S(stream));
-    if (rc != 1) {
-        if (rc || !dbias) return rc;
-        const long long M = (long long)n * d * h * w, rpb = 4096;
-        k_bias_grad<<<(unsigned)((M + rpb - 1) / rpb), 128, 0, S(stream)>>>(static_cast<const bf16*>(dy), M, cout,
-                                                                              dbias, rpb);
-        return check(cudaGetLastError(), "k_bias_grad launch");
-    }
     const long long M = (long long)n * d * h * w;
-    const int K = 27 * cin;
-    const long long vpb = 8192;
-    int nz = 0;
-    const int nf = pick_nf(cout, &nz);
-    const dim3 grid((unsigned)((K + BM - 1) / BM), (unsigned)((M + vpb - 1) / vpb), (unsigned)nz);
-    auto go = [&](auto kern) {
-        kern<<<grid, 128, 0, S(stream)>>>(static_cast<const bf16*>(x), static_cast<const bf16*>(dy), n, d, h, w, cin,
-                                          cout, wrap, dw, vpb);
-    };
-    switch (nf) {
-        case 1: go(k_wgrad<1>); break;
-        case 2: go(k_wgrad<2>); break;
-        case 4: go(k_wgrad<4>); break;
-        case 6: go(k_wgrad<6>); break;
-        case 8: go(k_wgrad<8>); break;
-        case 12: go(k_wgrad<12>); break;
-        default: go(k_wgrad<16>); break;
+    if (rc == 1) {
+        const int K = 27 * cin;
+        const long long vpb = 8192;
+        int nz = 0;
+        const int nf = pick_nf(cout, &nz);
+        const dim3 grid((unsigned)((K + BM - 1) / BM), (unsigned)((M + vpb - 1) / vpb), (unsigned)nz);
+        float* part = chunk_scratch((size_t)grid.y * K * cout);
+        if (!part) return fail(LBM_ERR_OOM, "weight-gradient partial sums");
+        auto go = [&](auto kern) {
+            kern<<<grid, 128, 0, S(stream)>>>(static_cast<const bf16*>(x), static_cast<const bf16*>(dy), n, d, h, w,
+                                              cin, cout, wrap, part, vpb);
+        };
+        switch (nf) {
+            case 1: go(k_wgrad<1>); break;
+            case 2: go(k_wgrad<2>); break;
+            case 4: go(k_wgrad<4>); break;
+            case 6: go(k_wgrad<6>); break;
+            case 8: go(k_wgrad<8>); break;
+            case 12: go(k_wgrad<12>); break;
+            default: go(k_wgrad<16>); break;
+        }
+        rc = check(cudaGetLastError(), "k_wgrad launch");
+        if (!rc) rc = sum_chunks(part, grid.y, (long long)K * cout, dw, S(stream));
     }
-    rc = check(cudaGetLastError(), "k_wgrad launch");
     if (rc || !dbias) return rc;
-    const long long rpb = 4096;
-    k_bias_grad<<<(unsigned)((M + rpb - 1) / rpb), 128, 0, S(stream)>>>(static_cast<const bf16*>(dy), M, cout, dbias,
-                                                                          rpb);
-    return check(cudaGetLastError(), "k_bias_grad launch");
+    const long long rpb = 4096, nb = (M + rpb - 1) / rpb;
+    float* part = chunk_scratch((size_t)nb * cout);  // the weight gradient's sums are already in dw
+    if (!part) return fail(LBM_ERR_OOM, "bias-gradient partial sums");
+    k_bias_grad<<<(unsigned)nb, 128, 0, S(stream)>>>(static_cast<const bf16*>(dy), M, cout, part, rpb);
+    rc = check(cudaGetLastError(), "k_bias_grad launch");
+    return rc ? rc : sum_chunks(part, nb, cout, dbias, S(stream));
 }
 
 extern "C" int lbm_nn_relu_mask(void* g, const void* act, size_t count, void* stream) {

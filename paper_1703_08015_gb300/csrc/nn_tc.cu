@@ -549,11 +549,13 @@ __global__ void k_wgrad_pack(const bf16* __restrict__ x, const bf16* __restrict_
 // covers up to 256 / Cp taps, one TMEM accumulator column range per tap.  The
 // two warps of each TMEM lane quadrant split the fills (taps of one parity
 // each) and the epilogue's column chunks; the three-stage ring and the bounded
-// waits are those of tc_pipeline.  The block's sums are added to dw
-// atomically.
+// waits are those of tc_pipeline.  The block's sums go to the partial sums of
+// its voxel chunk, part[blockIdx.x][tap][ci][co] (plain stores, NaN when a
+// wait ran out); k_sum_chunks adds the chunks to dw in a fixed order, so the
+// gradient does not depend on the order in which blocks finish.
 __global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const bf16* __restrict__ xp, const bf16* __restrict__ dyp, int Cin,
                                                   int Cp, int Cout, int Hp, int Wp, long long G, long long Lp,
-                                                  long long nsteps, long long spc, int TG, float* __restrict__ dw) {
+                                                  long long nsteps, long long spc, int TG, float* __restrict__ part) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t mbar[WG_STAGES];
     __shared__ uint32_t tmem_slot;
@@ -650,12 +652,12 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad_tc(const bf16* __restrict_
         for (int c0 = 16 * par; c0 < ntap * Cp; c0 += 32) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-            if (!ok || co >= Cout) continue;
+            if (co >= Cout) continue;
             const int t = c0 / Cp, ci0 = c0 - t * Cp;  // Cp % 16 == 0: one tap per 16 columns
-            float* dst = dw + ((size_t)(t0 + t) * Cin + ci0) * Cout + co;
+            float* dst = part + (size_t)blockIdx.x * 27 * Cin * Cout + ((size_t)(t0 + t) * Cin + ci0) * Cout + co;
 #pragma unroll
             for (int k = 0; k < 16; k++)
-                if (ci0 + k < Cin) atomicAdd(dst + (size_t)k * Cout, v[k]);
+                if (ci0 + k < Cin) dst[(size_t)k * Cout] = ok ? v[k] : __int_as_float(0x7fc00000);
         }
     tc::fence_before_sync();
     __syncthreads();
@@ -785,6 +787,42 @@ namespace nn {
 // process and grown on demand (calls on one stream reuse it in order).
 static unsigned char* g_wg_buf = nullptr;
 static size_t g_wg_bytes = 0;
+// Per-chunk partial sums of the weight gradients (k_wgrad_tc, k_wgrad,
+// k_bias_grad), summed in chunk order by k_sum_chunks: kept for the process
+// and grown on demand, like the packed operands.
+static float* g_part_buf = nullptr;
+static size_t g_part_floats = 0;
+
+float* chunk_scratch(size_t floats) {
+    if (floats > g_part_floats) {
+        if (g_part_buf) cudaFree(g_part_buf);
+        g_part_buf = nullptr;
+        g_part_floats = 0;
+        if (cudaMalloc(&g_part_buf, floats * sizeof(float)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g_part_buf = nullptr;
+            return nullptr;
+        }
+        g_part_floats = floats;
+    }
+    return g_part_buf;
+}
+
+// dst[e] += sum over c = 0 .. chunks-1 of part[c][e], in that order.
+__global__ void k_sum_chunks(const float* __restrict__ part, long long chunks, long long E, float* __restrict__ dst) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (long long c = 0; c < chunks; c++) s += part[c * E + e];
+        dst[e] += s;
+    }
+}
+
+int sum_chunks(const float* part, long long chunks, long long E, float* dst, cudaStream_t s) {
+    const long long blocks = (E + 255) / 256;
+    k_sum_chunks<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(part, chunks, E, dst);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_sum_chunks launch");
+}
 
 // dw += the weight gradient on the tensor cores (input channels padded to a
 // multiple of 16, 8 <= cin <= 256: below 8 the padding would multiply the
@@ -838,10 +876,14 @@ int wgrad_tc(const void* x, const void* dy, int n, int d, int h, int w, int cin,
     const uint32_t smem = WG_STAGES * (uint32_t)(TC_M * TC_BK * 2 + TG * cp * TC_BK * 2);
     rc = tc_launch_ok((const void*)k_wgrad_tc, smem, "cudaFuncSetAttribute(k_wgrad_tc)");
     if (rc) return rc;
+    const long long E = 27LL * cin * cout;
+    float* part = chunk_scratch((size_t)(chunks * E));
+    if (!part) return fail(LBM_ERR_OOM, "weight-gradient partial sums: %lld floats", chunks * E);
     k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), WG_THREADS, smem, s>>>(xpk, dypk, cin, cp, cout, Hp, Wp,
-                                                                                       G, Lp, nsteps, spc, TG, dw);
+                                                                                       G, Lp, nsteps, spc, TG, part);
     e = cudaGetLastError();
-    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_wgrad_tc launch");
+    if (e != cudaSuccess) return cuda_fail(e, "k_wgrad_tc launch");
+    return sum_chunks(part, chunks, E, dw, s);
 }
 }  // namespace nn
 }  // namespace lbm

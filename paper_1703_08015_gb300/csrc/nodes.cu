@@ -39,6 +39,13 @@ __global__ void k_init(const NodeArgs a) {
     const int stride = a.tile_stride[tile];
     T* out = static_cast<T*>(const_cast<void*>(a.pdf)) + a.tile_off[tile] +
              fluid_rank<TL::W>(a.tmask + (size_t)tile * TL::W, node);
+    if (!a.rho_in && !a.u_in) {  // the rest start: f^eq_i = w_i rho0 (Eq. 3 and Eq. 4 alike)
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            out[i * stride] = S::template from_f64<L, i>(Link<L, i>::w * a.rho0, a.f16_scale);
+        });
+        return;
+    }
     const double rho = a.rho_in ? a.rho_in[n] : a.rho0;
     const size_t N = (size_t)a.nx * a.ny * a.nz;
     const double ux = a.u_in ? a.u_in[n] : 0.0;
@@ -400,6 +407,43 @@ __global__ void k_average_f16(__half* __restrict__ cur, const __half* __restrict
 __global__ void k_fill_nan(double* p, size_t n) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
         p[k] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// ---- the step kernels' fluid-node list ---------------------------------------------------
+// nodes[first(k) + r] = k * NT + node for the r-th fluid node of tile k (row
+// order), first(k) = tile_off[k] / q (a tile's block holds q links of its nf
+// fluid nodes): the list the host would build, written where the tables are.
+template <class TL>
+__global__ void k_node_list(const uint64_t* __restrict__ tmask, const long long* __restrict__ tile_off, int q,
+                            uint32_t* __restrict__ nodes) {
+    const int tile = blockIdx.x;
+    const long long first = __ldg(tile_off + tile) / q;
+    for (int node = threadIdx.x; node < TL::NT; node += blockDim.x) {
+        if (!own_fluid<TL>(tmask, tile, node)) continue;
+        const int r = fluid_rank<TL::W>(tmask + (size_t)tile * TL::W, node);
+        nodes[first + r] = (uint32_t)tile * (uint32_t)TL::NT + (uint32_t)node;
+    }
+}
+
+template <class L, int A>
+cudaError_t launch_node_list(const uint64_t* tmask, const long long* tile_off, int n_tiles, uint32_t* nodes,
+                             cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    constexpr int NT = Tile<L, A>::NT;
+    k_node_list<Tile<L, A>><<<n_tiles, NT < 256 ? NT : 256, 0, s>>>(tmask, tile_off, L::Q, nodes);
+    return cudaGetLastError();
+}
+
+NodeListLaunch select_node_list(int lattice, int a) {
+    if (lattice == LBM_D2Q9) {
+        if (a == 8) return &launch_node_list<D2Q9, 8>;
+        if (a == 16) return &launch_node_list<D2Q9, 16>;
+        if (a == 32) return &launch_node_list<D2Q9, 32>;
+    } else if (lattice == LBM_D3Q19) {
+        if (a == 4) return &launch_node_list<D3Q19, 4>;
+        if (a == 8) return &launch_node_list<D3Q19, 8>;
+    }
+    return nullptr;
 }
 
 // ---- launchers ------------------------------------------------------------------------

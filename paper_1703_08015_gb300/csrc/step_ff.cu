@@ -15,8 +15,9 @@
 //     ulp(w_c) (the scale is folded into the constants), and every f*_i is
 //     rounded once to FP64: the integer count of ulps is taken within one unit
 //     of the float-float result.
-// Nodes outside that range (|f_i - w_i| beyond ~w_i/32, |j| >= 1/16,
-// |rho - 1| >= 1/32, NaN, negative values) are recomputed in native FP64.
+// Nodes outside that range (|f_i - w_i| beyond ~w_i/32, a result beyond
+// ~w_i/64, |j| >= 1/16, |rho - 1| >= 1/32, NaN, negative values) are
+// recomputed in native FP64.
 #include <cmath>
 
 #include "collide_ff.cuh"
@@ -204,6 +205,10 @@ static void ff_consts_for(const lbm_params* p, FFConsts* k) {
     k->w12 = lanes(k->w[1], k->w[2]);
     k->rho12 = lanes(k->rho[1], k->rho[2]);
     k->kf01 = lanes(k->kf[0], k->kf[1]);
+    k->w11 = lanes(k->w[1], k->w[1]);
+    k->w22 = lanes(k->w[2], k->w[2]);
+    k->rho11 = lanes(k->rho[1], k->rho[1]);
+    k->rho22 = lanes(k->rho[2], k->rho[2]);
     for (int g = 0; g < FFGroups<L>::n; g++) {
         const int a = FFGroups<L>::a[g], b = FFGroups<L>::b[g];
         k->beta2[g] = lanes(k->beta[a], k->beta[b]);

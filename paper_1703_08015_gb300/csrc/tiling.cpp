@@ -12,6 +12,7 @@
 // row order), so solid nodes of porous tiles cost neither memory nor
 // bandwidth; a node's slot is its rank among the tile's fluid nodes.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -126,74 +127,112 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     T->tmask.clear();
     T->coords.clear();
 
-    // fluid bits and counts of every tile, tile rows (tz, ty) in parallel
+    // fluid bits and counts of every tile, tile rows (tz, ty) in parallel: each
+    // mask row is read once, left to right, its nodes' bits set in the tiles
+    // they fall in (node lx + a (ly + a lz) of the tile)
     const int W = T->words;
+    int la = 0;
+    while ((1 << la) < a) la++;  // a is a power of two (checked by validate_params)
     std::vector<uint64_t> all_bits((size_t)n_tiles64 * W, 0ull);
     std::vector<int32_t> all_nf((size_t)n_tiles64, 0);
     parallel_ranges((int64_t)ntz * nty, 8, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; r++) {
             const int tz = (int)(r / nty), ty = (int)(r % nty);
-            for (int tx = 0; tx < ntx; tx++) {
-                const size_t t = ((size_t)tz * nty + ty) * ntx + tx;
-                uint64_t* bits = &all_bits[t * W];
-                int nf = 0;
-                for (int lz = 0; lz < az; lz++) {
-                    const int z = tz * az + lz;
-                    if (z >= nz) break;
-                    for (int ly = 0; ly < a; ly++) {
-                        const int y = ty * a + ly;
-                        if (y >= ny) break;
-                        const uint8_t* row = mask + ((size_t)z * ny + y) * nx;
-                        for (int lx = 0; lx < a; lx++) {
-                            const int x = tx * a + lx;
-                            if (x >= nx) break;
-                            if (row[x]) {
-                                const int node = lx + a * (ly + a * lz);
-                                bits[node >> 6] |= 1ull << (node & 63);
-                                nf++;
-                            }
+            uint64_t* bits = &all_bits[(size_t)r * ntx * W];
+            for (int lz = 0; lz < az; lz++) {
+                const int z = tz * az + lz;
+                if (z >= nz) break;
+                for (int ly = 0; ly < a; ly++) {
+                    const int y = ty * a + ly;
+                    if (y >= ny) break;
+                    const uint8_t* row = mask + ((size_t)z * ny + y) * nx;
+                    const int base = a * (ly + a * lz);  // node index of lx = 0
+                    int x = 0;
+                    // eight mask bytes at a time: one bit per nonzero byte
+                    // (x = 8k: the eight nodes lie in one tile for a >= 8, in
+                    // two consecutive tiles for a = 4)
+                    for (; x + 8 <= nx; x += 8) {
+                        uint64_t v;
+                        std::memcpy(&v, row + x, 8);
+                        if (!v) continue;
+                        const uint64_t hi = ((v & 0x7F7F7F7F7F7F7F7Full) + 0x7F7F7F7F7F7F7F7Full) | v;
+                        const uint64_t b8 = (((hi & 0x8080808080808080ull) >> 7) * 0x0102040810204080ull) >> 56;
+                        for (int h = 0; h < 8; h += a < 8 ? a : 8) {
+                            const uint64_t part = (b8 >> h) & (a < 8 ? (1ull << a) - 1 : 0xFFull);
+                            if (!part) continue;
+                            const int node = base + ((x + h) & (a - 1));
+                            bits[(size_t)((x + h) >> la) * W + (node >> 6)] |= part << (node & 63);
                         }
                     }
+                    for (; x < nx; x++) {
+                        if (!row[x]) continue;
+                        const int node = base + (x & (a - 1));
+                        bits[(size_t)(x >> la) * W + (node >> 6)] |= 1ull << (node & 63);
+                    }
                 }
-                all_nf[t] = nf;
+            }
+            for (int tx = 0; tx < ntx; tx++) {
+                int nf = 0;
+                for (int w = 0; w < W; w++) nf += __builtin_popcountll(bits[(size_t)tx * W + w]);
+                all_nf[(size_t)r * ntx + tx] = nf;
             }
         }
     });
-    // ranks in row-major scan order (serial: the tile index is a prefix count)
-    int32_t count = 0;
-    int64_t n_fluid = 0;
-    for (int tz = 0; tz < ntz; tz++)
-        for (int ty = 0; ty < nty; ty++)
+    // ranks in row-major scan order: the tile index is a prefix count over the
+    // tiles, taken per tile row in parallel, then the rows' offsets
+    const int64_t n_rows = (int64_t)ntz * nty;
+    std::vector<int32_t> row_count((size_t)n_rows + 1, 0);
+    std::vector<int64_t> row_fluid((size_t)n_rows + 1, 0);
+    parallel_ranges(n_rows, 64, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; r++) {
+            int c = 0;
+            int64_t f = 0;
             for (int tx = 0; tx < ntx; tx++) {
-                const size_t t = ((size_t)tz * nty + ty) * ntx + tx;
-                if (!all_nf[t]) continue;
-                T->tile_map[t] = count++;
-                n_fluid += all_nf[t];
+                const int32_t nf = all_nf[(size_t)r * ntx + tx];
+                c += nf > 0;
+                f += nf;
             }
+            row_count[r + 1] = c;
+            row_fluid[r + 1] = f;
+        }
+    });
+    for (int64_t r = 0; r < n_rows; r++) {
+        row_count[r + 1] += row_count[r];
+        row_fluid[r + 1] += row_fluid[r];
+    }
+    const int32_t count = row_count[n_rows];
+    const int64_t n_fluid = row_fluid[n_rows];
     T->tmask.resize((size_t)count * W);
     T->coords.resize((size_t)count * 3);
-    for (size_t t = 0; t < (size_t)n_tiles64; t++) {
-        const int32_t k = T->tile_map[t];
-        if (k < 0) continue;
-        std::memcpy(&T->tmask[(size_t)k * W], &all_bits[t * W], (size_t)W * sizeof(uint64_t));
-        T->coords[(size_t)3 * k] = (int)(t % ntx);
-        T->coords[(size_t)3 * k + 1] = (int)((t / ntx) % nty);
-        T->coords[(size_t)3 * k + 2] = (int)(t / ((size_t)ntx * nty));
-    }
+    parallel_ranges(n_rows, 64, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; r++) {
+            int32_t k = row_count[r];
+            for (int tx = 0; tx < ntx; tx++) {
+                const size_t t = (size_t)r * ntx + tx;
+                if (!all_nf[t]) continue;
+                T->tile_map[t] = k;
+                std::memcpy(&T->tmask[(size_t)k * W], &all_bits[t * W], (size_t)W * sizeof(uint64_t));
+                T->coords[(size_t)3 * k] = tx;
+                T->coords[(size_t)3 * k + 1] = (int)(r % nty);
+                T->coords[(size_t)3 * k + 2] = (int)(r / nty);
+                k++;
+            }
+        }
+    });
 
+    // neighbour records through a tile map padded by one tile on each side:
+    // the pad holds the wrapped tile on a periodic axis, -1 beyond a wall
     const int per[3] = {p->periodic[0] ? 1 : 0, p->periodic[1] ? 1 : 0, d == 3 && p->periodic[2] ? 1 : 0};
     const int ntv[3] = {ntx, nty, ntz};
-    T->nbr.resize((size_t)count * T->nn);
-    parallel_ranges(count, 1024, [&](int64_t k0, int64_t k1) {
-    for (int64_t k = k0; k < k1; k++) {
-        const int* c = &T->coords[(size_t)3 * k];
-        int slot = 0;
-        for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++, slot++) {
-                    int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+    const int px = ntx + 2, py = nty + 2, pz = d == 3 ? ntz + 2 : 1;
+    std::vector<int32_t> pmap((size_t)px * py * pz, -1);
+    parallel_ranges(pz, 4, [&](int64_t z0, int64_t z1) {
+        for (int64_t zz = z0; zz < z1; zz++)
+            for (int yy = 0; yy < py; yy++)
+                for (int xx = 0; xx < px; xx++) {
+                    int q[3] = {xx - 1, yy - 1, d == 3 ? (int)zz - 1 : 0};
                     bool ok = true;
-                    for (int ax = 0; ax < 3; ax++) {
+                    for (int ax = 0; ax < d; ax++) {
                         if (q[ax] < 0 || q[ax] >= ntv[ax]) {
                             if (per[ax])
                                 q[ax] = (q[ax] + ntv[ax]) % ntv[ax];
@@ -201,10 +240,25 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
                                 ok = false;
                         }
                     }
-                    T->nbr[(size_t)k * T->nn + slot] =
+                    pmap[((size_t)zz * py + yy) * px + xx] =
                         ok ? T->tile_map[((size_t)q[2] * nty + q[1]) * ntx + q[0]] : -1;
                 }
+    });
+    int64_t off[27];
+    {
+        int slot = 0;
+        for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++, slot++) off[slot] = ((int64_t)dz * py + dy) * px + dx;
     }
+    T->nbr.resize((size_t)count * T->nn);
+    parallel_ranges(count, 1024, [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; k++) {
+            const int* c = &T->coords[(size_t)3 * k];
+            const int64_t centre = ((int64_t)(d == 3 ? c[2] + 1 : 0) * py + (c[1] + 1)) * px + (c[0] + 1);
+            int32_t* out = &T->nbr[(size_t)k * T->nn];
+            for (int slot = 0; slot < T->nn; slot++) out[slot] = pmap[(size_t)(centre + off[slot])];
+        }
     });
 
     // Compact layout: a tile stores only its fluid nodes, in row order, link
@@ -225,12 +279,16 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
 
     // the step kernels address a tile's neighbours with 32-bit value offsets
     // from the first tile of their block: neighbours must lie within 2^30 values
-    for (int32_t k = 0; k < count; k++)
-        for (int slot = 0; slot < T->nn; slot++) {
-            const int32_t nb = T->nbr[(size_t)k * T->nn + slot];
-            if (nb >= 0 && std::llabs(T->tile_off[nb] - T->tile_off[k]) > (1ll << 30))
-                return fail(LBM_ERR_CAPACITY, "neighbour tiles lie more than 2^30 values apart (tile plane too large)");
-        }
+    std::atomic<bool> far{false};
+    parallel_ranges(count, 4096, [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1 && !far.load(std::memory_order_relaxed); k++)
+            for (int slot = 0; slot < T->nn; slot++) {
+                const int32_t nb = T->nbr[(size_t)k * T->nn + slot];
+                if (nb >= 0 && std::llabs(T->tile_off[nb] - T->tile_off[k]) > (1ll << 30))
+                    far.store(true, std::memory_order_relaxed);
+            }
+    });
+    if (far.load()) return fail(LBM_ERR_CAPACITY, "neighbour tiles lie more than 2^30 values apart (tile plane too large)");
 
     lbm_tiling& I = T->info;
     I.ntx = ntx;
@@ -307,7 +365,7 @@ int work_threads_for(int lattice, int a) {
 
 // Fluid nodes in tile-major, row order, cut into blocks of consecutive tiles
 // holding at most `threads` nodes and `max_tiles` tiles.
-void build_work_list(HostTiling* T, int threads, int max_tiles) {
+long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes) {
     const int nt = T->d == 3 ? T->a * T->a * T->a : T->a * T->a;
     const int32_t n = T->info.n_ftiles;
     T->nodes.clear();
@@ -335,6 +393,7 @@ void build_work_list(HostTiling* T, int threads, int max_tiles) {
         cur.n_tiles++;
     }
     if (cur.n_tiles > 0) T->blocks.push_back(cur);
+    if (!want_nodes) return first[n];
     // the nodes of each tile in row order, tiles in parallel
     T->nodes.resize((size_t)first[n]);
     parallel_ranges(n, 1024, [&](int64_t k0, int64_t k1) {
@@ -345,6 +404,7 @@ void build_work_list(HostTiling* T, int threads, int max_tiles) {
                 if ((m[node >> 6] >> (node & 63)) & 1ull) *out++ = (uint32_t)k * (uint32_t)nt + node;
         }
     });
+    return first[n];
 }
 
 }  // namespace lbm

@@ -638,14 +638,18 @@ def predict_fields(net, mask, force, nu):
 
 
 def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F64, target=1e-6, check_every=100,
-                   max_steps=60000, filter_period2=True, device="cuda"):
+                   max_steps=60000, filter_period2=True, finish=None, stall_checks=10, device="cuda"):
     """Wall time and steps until the LBM residual (relative change of u over
     check_every steps) falls below target, from rest or from the network's
     prediction; the timed region includes tiling, initialisation and network
     inference.  With filter_period2 the state is replaced by the mean of two
     consecutive states after every residual check that has not converged
-    (lbm_filter_period2).  Returns a dict (converged, steps, seconds,
-    permeability, velocity field on the fluid nodes)."""
+    (lbm_filter_period2).  With `finish` (a storage form), a run whose residual
+    stops falling (no 5 % gain over `stall_checks` checks: the rounding floor
+    of a reduced storage form) continues from its state in that storage; the
+    residual of the finishing form still decides convergence.  Returns a dict
+    (converged, steps, seconds, permeability, velocity field on the fluid
+    nodes, steps taken before the switch)."""
     import torch
 
     dev = torch.device(device)
@@ -658,13 +662,26 @@ def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F6
     s = lbm.Solver(mask, lbm.LBM_D3Q19, 4, (1, 0, 0), tau, (force, 0, 0), storage=storage, rho_init=rho0,
                    u_init=u0, device=dev)
     s.stats(residual=True)
-    n, st, rc = 0, None, 0
+    n, st, rc, hist, switched_at, floor = 0, None, 0, [], None, None
     while n < max_steps:
         s.step(check_every)
         n += check_every
         st, rc = s.stats(residual=True)
         if rc != 0 or st.residual < target:
             break
+        hist.append(st.residual)
+        if (finish is not None and switched_at is None and len(hist) > stall_checks
+                and hist[-1] > 0.95 * hist[-1 - stall_checks]):
+            # the reduced form has reached its floor: carry the state over
+            pdfs = torch.empty((19,) + mask.shape, dtype=torch.float64, device=dev)
+            lbm.lbm_export_pdfs(s.ctx, pdfs, lbm.LBM_OUT_DEVICE, s._s())
+            s2 = lbm.Solver(mask, lbm.LBM_D3Q19, 4, (1, 0, 0), tau, (force, 0, 0), storage=finish, device=dev)
+            lbm.lbm_import_pdfs(s2.ctx, pdfs, n, lbm.LBM_OUT_DEVICE, s2._s())
+            s.close()
+            del pdfs
+            s, switched_at, floor = s2, n, min(hist)
+            s.stats(residual=True)
+            continue
         if filter_period2:
             s.filter_period2()
     torch.cuda.synchronize(dev)
@@ -674,7 +691,7 @@ def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F6
     fl = mask.astype(bool)
     return {"converged": bool(rc == 0 and st.residual < target), "steps": n, "seconds": dt,
             "residual": float(st.residual), "permeability": nu * float(np.sum(u[0][fl])) / mask.size / force,
-            "u": u[:, fl], "status": int(rc)}
+            "u": u[:, fl], "status": int(rc), "switched_at": switched_at, "residual_floor_before_switch": floor}
 
 
 def solve_to_steady(mask, net=None, **kw):

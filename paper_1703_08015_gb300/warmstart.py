@@ -48,13 +48,14 @@ def evaluate(net, masks, cases, tau=0.6, force=1e-6, target=1e-6, max_steps=1500
         row = {"fluid_fraction": float(m.mean())}
         fl = m.astype(bool)
         fields = {}
-        for label, form, start, filt in cases:
+        for label, form, start, filt, *fin in cases:
             r = nn.solve_to_steady(m, net if start == "warm" else None, tau=tau, force=force,
                                    storage=STORAGES[form], target=target, max_steps=max_steps,
-                                   filter_period2=filt, device=device)
+                                   filter_period2=filt, finish=STORAGES[fin[0]] if fin else None,
+                                   device=device)
             fields[label] = r.pop("u")
             row[label] = r
-        ref_label = next(lb for lb, _, st, f in cases if st == "zero" and f)
+        ref_label = next(c[0] for c in cases if c[2] == "zero" and c[3])
         u_ref, k_ref = fields[ref_label], row[ref_label]["permeability"]
         nrm = float(np.sqrt(np.sum(u_ref * u_ref)))
         for label in fields:
@@ -68,7 +69,7 @@ def evaluate(net, masks, cases, tau=0.6, force=1e-6, target=1e-6, max_steps=1500
         row["prediction_permeability_rel_err"] = abs(k_pred / k_ref - 1.0)
         rows.append(row)
         if log:
-            s = ", ".join(f"{lb} {row[lb]['steps']}" for lb, *_ in cases)
+            s = ", ".join(f"{c[0]} {row[c[0]]['steps']}" for c in cases)
             log(f"held-out {k + 1}/{len(masks)} fluid {row['fluid_fraction']:.2f}: {s}; "
                 f"prediction error u {row['prediction_u_rel_l2']:.3f}")
     return rows
@@ -84,14 +85,15 @@ def summarize(rows, cases):
     if not ok:
         return out
     tot = {lb: sum(r[lb]["seconds"] for r in ok) for lb in labels}
-    for lb, form, start, filt in cases:
+    for lb, form, start, filt, *_ in cases:
         steps = np.array([r[lb]["steps"] for r in ok])
         e = {"converged": sum(r[lb]["converged"] for r in rows), "steps_median": float(np.median(steps)),
              "steps_mean": float(steps.mean()), "seconds_total": tot[lb],
              "speedup_vs_" + labels[0]: tot[labels[0]] / tot[lb],
              "u_rel_err_median": float(np.median([r[lb]["u_rel_err"] for r in ok])),
              "permeability_rel_err_max": max(r[lb]["permeability_rel_err"] for r in ok),
-             "fallbacks": sum(bool(r[lb].get("fallback")) for r in rows)}
+             "fallbacks": sum(bool(r[lb].get("fallback")) for r in rows),
+             "switched": sum(r[lb].get("switched_at") is not None for r in rows)}
         zero = f"{form}_zero"
         if start == "warm" and zero in labels:
             ratio = np.array([r[lb]["steps"] / r[zero]["steps"] for r in ok])

@@ -388,3 +388,32 @@ def test_training_reduces_loss(nn):
         net.backward(dout)
         net.adam(3e-3)
     assert hist[-1] < 0.5 * hist[0]
+
+
+def test_training_is_deterministic(nn):
+    """Two nets from the same seed, trained on the same batches, end with the
+    same bits: every gradient (weights and biases, through the tcgen05 and the
+    gather weight-gradient kernels) sums its voxel chunks in a fixed order."""
+    rng = np.random.default_rng(19)
+    n, s = 2, 16
+    masks = torch.from_numpy((rng.uniform(size=(n, s, s, s)) < 0.6).astype(np.uint8)).cuda()
+    tgt = torch.from_numpy(rng.normal(size=(n, s, s, s, 4)).astype(np.float32)).cuda()
+    count = int(masks.sum().item())
+    states = []
+    for _ in range(2):
+        net = nn.UNet((16, 32), cin=2, cout=4, wrap=1, seed=3)
+        x = nn.inputs_from_masks(masks, 1e-6, net._s())
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for it in range(4):
+            y = net.forward(x, (n, s, s, s), keep=True)
+            dout = torch.empty(y.shape, dtype=torch.bfloat16, device="cuda")
+            nn.lbm_nn_mse(y, tgt, masks, n * s ** 3, 4, count, loss, dout, net._s())
+            net.backward(dout)
+            net.adam(1e-3)
+        torch.cuda.synchronize()
+        # FP32 master weights and biases, their BF16 copy, Adam's moments
+        states.append([t.detach().contiguous().view(torch.uint8).cpu().numpy().copy()
+                       for t in (net.p, net.pb, net.m, net.v)])
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
+    assert nn.lbm_nn_tc_timeouts() == 0
