@@ -362,8 +362,12 @@ int lbm_num_samples(const lbm_ctx* ctx);
 /* Counts of the context's tiling (see lbm_tiling).  Errors: LBM_ERR_ARG. */
 int lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out);
 
-/* Release the context and the tables lbm_init allocated (never the caller's
- * PDF buffers).  Waits for the context's pending work.  NULL is accepted. */
+/* Release the context and the tables lbm_init allocated for it -- the tile
+ * map, neighbour records and node types of Sec. 3 / Fig. 5, the work list,
+ * the reduction partials -- but never the caller's PDF buffers.  Waits for
+ * the context's pending work (cudaDeviceSynchronize).  NULL is accepted.
+ * Errors: LBM_ERR_CUDA (a pending kernel failed; the context is still
+ * released). */
 int lbm_free(lbm_ctx* ctx);
 
 /* Message describing the last failure on the calling host thread. */
