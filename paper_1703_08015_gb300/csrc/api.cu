@@ -154,8 +154,8 @@ static void release(lbm_ctx* c) {
     delete c;
 }
 
-template <class T>
-static int upload(T** dst, const std::vector<T>& v, cudaStream_t s) {
+template <class T, class Alloc>
+static int upload(T** dst, const std::vector<T, Alloc>& v, cudaStream_t s) {
     const size_t bytes = (v.empty() ? 1 : v.size()) * sizeof(T);
     LBM_CUDA_TRY(cudaMalloc(dst, bytes));
     if (!v.empty()) LBM_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
@@ -29,13 +31,37 @@ struct WorkBlock {
 };
 
 // ---- host tiling ------------------------------------------------------------
+// An allocator whose default construction leaves trivial elements as they
+// are: resize() of a vector the tiling then fills completely (in parallel)
+// skips a serial zero fill and its first-touch page faults.
+template <class T>
+struct fill_later_alloc : std::allocator<T> {
+    fill_later_alloc() = default;
+    template <class U>
+    fill_later_alloc(const fill_later_alloc<U>&) noexcept {}
+    template <class U>
+    struct rebind {
+        using other = fill_later_alloc<U>;
+    };
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <class U, class... Args>
+    void construct(U* p, Args&&... args) {
+        ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+    }
+};
+template <class T>
+using fill_vector = std::vector<T, fill_later_alloc<T>>;
+
 struct HostTiling {
     lbm_tiling info{};
     int a = 0, d = 0, nn = 0, words = 0;     // edge, dimension, 3^d, mask words per tile
     std::vector<int32_t> tile_map;           // [n_tiles]
-    std::vector<int32_t> nbr;                // [n_ftiles][nn]
-    std::vector<uint64_t> tmask;             // [n_ftiles][words], bit n = node n fluid
-    std::vector<int32_t> coords;             // [n_ftiles][3] tile coordinates
+    fill_vector<int32_t> nbr;                // [n_ftiles][nn]
+    fill_vector<uint64_t> tmask;             // [n_ftiles][words], bit n = node n fluid
+    fill_vector<int32_t> coords;             // [n_ftiles][3] tile coordinates
     std::vector<long long> tile_off;         // [n_ftiles] first value of the tile's PDF block
     std::vector<int32_t> tile_stride;        // [n_ftiles] values per link (fluid count, sector-padded)
     std::vector<uint32_t> nodes;             // fluid nodes, tile-major: tile * NT + node

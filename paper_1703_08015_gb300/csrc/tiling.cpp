@@ -133,12 +133,13 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     const int W = T->words;
     int la = 0;
     while ((1 << la) < a) la++;  // a is a power of two (checked by validate_params)
-    std::vector<uint64_t> all_bits((size_t)n_tiles64 * W, 0ull);
-    std::vector<int32_t> all_nf((size_t)n_tiles64, 0);
+    fill_vector<uint64_t> all_bits((size_t)n_tiles64 * W);  // zeroed row by row below
+    fill_vector<int32_t> all_nf((size_t)n_tiles64);
     parallel_ranges((int64_t)ntz * nty, 8, [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; r++) {
             const int tz = (int)(r / nty), ty = (int)(r % nty);
             uint64_t* bits = &all_bits[(size_t)r * ntx * W];
+            std::memset(bits, 0, (size_t)ntx * W * sizeof(uint64_t));
             for (int lz = 0; lz < az; lz++) {
                 const int z = tz * az + lz;
                 if (z >= nz) break;
@@ -264,23 +265,34 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     // Compact layout: a tile stores only its fluid nodes, in row order, link
     // after link with no padding (contiguous link arrays fill whole sectors).
     const int bpv = (int)bytes_per_value(p->storage);
-    const int pad = 1;
+    constexpr int pad = 1;
+    // (pad = 1: a tile's stride is its fluid count, so the offsets are q times
+    // the prefix counts of fluid nodes, taken per tile row from the row sums)
     T->tile_off.resize(count);
     T->tile_stride.resize(count);
-    long long total = 0;
-    for (int32_t k = 0; k < count; k++) {
-        int nf = 0;
-        for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(T->tmask[(size_t)k * T->words + w]);
-        const int stride = (nf + pad - 1) / pad * pad;
-        T->tile_off[k] = total;
-        T->tile_stride[k] = stride;
-        total += (long long)lattice_q(p->lattice) * stride;
-    }
+    const int q = lattice_q(p->lattice);
+    static_assert(pad == 1, "offsets from the fluid prefix counts assume no padding");
+    parallel_ranges(n_rows, 64, [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; r++) {
+            int32_t k = row_count[r];
+            long long off = (long long)q * row_fluid[r];
+            for (int tx = 0; tx < ntx; tx++) {
+                const int32_t nf = all_nf[(size_t)r * ntx + tx];
+                if (!nf) continue;
+                T->tile_off[k] = off;
+                T->tile_stride[k] = nf;
+                off += (long long)q * nf;
+                k++;
+            }
+        }
+    });
+    const long long total = (long long)q * n_fluid;
 
     // the step kernels address a tile's neighbours with 32-bit value offsets
-    // from the first tile of their block: neighbours must lie within 2^30 values
+    // from the first tile of their block: neighbours must lie within 2^30
+    // values (always so when the whole copy holds fewer values)
     std::atomic<bool> far{false};
-    parallel_ranges(count, 4096, [&](int64_t k0, int64_t k1) {
+    if (total > (1ll << 30)) parallel_ranges(count, 4096, [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1 && !far.load(std::memory_order_relaxed); k++)
             for (int slot = 0; slot < T->nn; slot++) {
                 const int32_t nb = T->nbr[(size_t)k * T->nn + slot];
