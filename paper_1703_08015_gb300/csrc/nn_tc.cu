@@ -283,8 +283,53 @@ __device__ __forceinline__ int halo_nb(int c, int n, bool wrap) {
     return (c < 0 || c >= n) ? -1 : c;
 }
 
+// The weights of the halo-tile convolution as the B stages it streams: for
+// output-channel tile ty (NT channels from ty * NT) and global stage gs (the
+// stages of input-channel chunk cb = 0, HCC, .. in order, 27 cc / TC_BK
+// rounded up per chunk of cc channels), the stage's NT x TC_BK operand in its
+// shared-memory layout (K-major core matrices, tile_off), element (co, kk) =
+// wgt[tap][cb + ci][ty NT + co] for k = (stage within chunk) TC_BK + kk = tap
+// cc + ci, zero past the chunk's 27 cc rows or past Cout.  One thread per
+// 16-byte core-matrix row (8 consecutive kk of one co).
+__global__ void k_pack_weights(const bf16* __restrict__ wgt, int Cin, int Cout, int NT, int G_total,
+                               unsigned char* __restrict__ wpack) {
+    const uint32_t bstage = (uint32_t)NT * TC_BK * 2;
+    const long long units = (long long)bstage / 16;  // per stage
+    const long long total = (long long)((Cout + NT - 1) / NT) * G_total * units;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long u = e % units, stage = e / units;
+        const int gs = (int)(stage % G_total), ty = (int)(stage / G_total);
+        // chunk and stage within it
+        int cb = 0, kc = gs;
+        for (;;) {
+            const int cc = Cin - cb < HCC ? Cin - cb : HCC;
+            const int nk = (27 * cc + TC_BK - 1) / TC_BK;
+            if (kc < nk) break;
+            kc -= nk;
+            cb += HCC;
+        }
+        const int cc = Cin - cb < HCC ? Cin - cb : HCC;
+        const int c8 = (int)(u / (TC_BK / 8)) , gk = (int)(u % (TC_BK / 8));  // row co = c8, k-group gk
+        const int co = ty * NT + c8;
+        uint4 out;
+        bf16* h = reinterpret_cast<bf16*>(&out);
+#pragma unroll
+        for (int col = 0; col < 8; col++) {
+            const int k = kc * TC_BK + gk * 8 + col;
+            bf16 v = __float2bfloat16(0.f);
+            if (k < 27 * cc && co < Cout) {
+                const int tap = k / cc, ci = k - tap * cc;
+                v = wgt[((size_t)tap * Cin + cb + ci) * Cout + co];
+            }
+            h[col] = v;
+        }
+        *reinterpret_cast<uint4*>(wpack + (size_t)stage * bstage + tc::tile_off(c8, gk, TC_KGAP, TC_RGAP)) = out;
+    }
+}
+
 __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, int N, int D, int H, int W, int Cin,
-                                                   const bf16* __restrict__ wgt, const float* __restrict__ bias,
+                                                   const unsigned char* __restrict__ wpack, int G_total,
+                                                   const float* __restrict__ bias,
                                                    int Cout, int NT, int MB, int relu, int wrap,
                                                    bf16* __restrict__ y, float* __restrict__ y32) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -322,23 +367,12 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
     bool ok = true;
     int g = 0;  // stages issued by the block so far (selects the ring buffer and mbarrier phase)
 
-    // B[co][k] of chunk k = tap * cc + ci (ci < cc) from wgt[tap][cb + ci][c0 + co]
-    auto fill_b = [&](unsigned char* sb, int cb, int cc, int kc) {
-        const int kk_n = 27 * cc;
-        for (int e = tid; e < TC_BK * (NT / 8); e += 128) {
-            const int kk = e / (NT / 8), c8 = (e - kk * (NT / 8)) * 8;
-            const int k = kc * TC_BK + kk;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (k < kk_n && c0 + c8 < Cout) {
-                const int tap = k / cc, ci = k - tap * cc;
-                v = *reinterpret_cast<const uint4*>(wgt + ((size_t)tap * Cin + cb + ci) * Cout + c0 + c8);
-            }
-            const bf16* h = reinterpret_cast<const bf16*>(&v);
-            const int gk = kk >> 3, col = kk & 7;
-#pragma unroll
-            for (int j = 0; j < 8; j++)
-                *reinterpret_cast<bf16*>(sb + tc::tile_off(c8 + j, gk, TC_KGAP, TC_RGAP) + col * 2) = h[j];
-        }
+    // B stage number gs of this block's channel tile (k_pack_weights wrote it
+    // in its shared-memory layout): one 16-byte copy per core-matrix row
+    const unsigned char* const wtile = wpack + (size_t)blockIdx.y * G_total * bstage;
+    auto fill_b = [&](unsigned char* sb, int gs) {
+        const unsigned char* src = wtile + (size_t)gs * bstage;
+        for (uint32_t e = tid; e < bstage / 16; e += 128) tc::cp_async16(sb + e * 16, src + e * 16, true);
     };
 
     for (int cb = 0; cb < Cin; cb += HCC) {
@@ -360,7 +394,7 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
         }
         // the ring's first stages join the tile's copies in the first group
         for (int p = 0; p < TC_STAGES - 1; p++) {
-            if (p < nk) fill_b(ring + ((g + p) % TC_STAGES) * bstage, cb, cc, p);
+            if (p < nk) fill_b(ring + ((g + p) % TC_STAGES) * bstage, g + p);
             tc::cp_async_commit();
         }
         for (int kc = 0; kc < nk; kc++, g++) {
@@ -389,7 +423,7 @@ __global__ void __launch_bounds__(128) k_conv_halo(const bf16* __restrict__ x, i
             if (nxt < nk) {
                 const int r = (g + TC_STAGES - 1) % TC_STAGES;
                 if (kc >= 1) ok &= tc::mbar_wait(&mbar[r], ((g - 1) / TC_STAGES) & 1, TC_WAIT);
-                fill_b(ring + r * bstage, cb, cc, nxt);
+                fill_b(ring + r * bstage, g + TC_STAGES - 1);
             }
             tc::cp_async_commit();
         }
@@ -718,6 +752,10 @@ int conv3d_tc(const void* x, int n, int d, int h, int w, int cin, const void* wg
 namespace lbm {
 namespace nn {
 static int g_halo_mb = 0, g_halo_nt = 0;  // fixed by lbm_nn_conv_tune; 0 = chosen per shape
+// The halo-tile convolution's weights packed as B stages (k_pack_weights):
+// kept for the process, grown on demand; calls on one stream reuse it in order.
+static unsigned char* g_wpack = nullptr;
+static size_t g_wpack_bytes = 0;
 
 static int sm_count() {
     static int sms = 0;
@@ -772,10 +810,30 @@ int conv3d_halo(const void* x, int n, int d, int h, int w, int cin, const void* 
     const uint32_t smem = halo_smem_bytes(cin, nt, mb);
     int rc = tc_launch_ok((const void*)k_conv_halo, smem, "cudaFuncSetAttribute(k_conv_halo)");
     if (rc) return rc;
+    // the weights as the blocks' B stages (a library-owned buffer, repacked per call)
+    int G_total = 0;
+    for (int cb = 0; cb < cin; cb += HCC) G_total += (27 * (cin - cb < HCC ? cin - cb : HCC) + TC_BK - 1) / TC_BK;
+    const size_t pack_bytes = (size_t)gy * G_total * nt * TC_BK * 2;
+    if (pack_bytes > g_wpack_bytes) {
+        if (g_wpack) cudaFree(g_wpack);
+        g_wpack = nullptr;
+        g_wpack_bytes = 0;
+        if (cudaMalloc(&g_wpack, pack_bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            g_wpack = nullptr;
+            return 1;  // no room: the other kernels need no packed weights
+        }
+        g_wpack_bytes = pack_bytes;
+    }
+    const long long units = (long long)pack_bytes / 16;
+    k_pack_weights<<<(unsigned)((units + 127) / 128 < 1216 ? (units + 127) / 128 : 1216), 128, 0, s>>>(
+        static_cast<const bf16*>(wgt), cin, cout, nt, G_total, g_wpack);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_pack_weights launch");
     k_conv_halo<<<dim3((unsigned)blocks, (unsigned)gy), 128, smem, s>>>(
-        static_cast<const bf16*>(x), n, d, h, w, cin, static_cast<const bf16*>(wgt), bias, cout, nt, mb, relu, wrap,
+        static_cast<const bf16*>(x), n, d, h, w, cin, g_wpack, G_total, bias, cout, nt, mb, relu, wrap,
         static_cast<bf16*>(y), y32);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "k_conv_halo launch");
 }
 }  // namespace nn
