@@ -244,8 +244,10 @@ def step_kernel_name(lat, a, storage, layout, arith_name):
         store = {"f32": "StoreF32", "f32s": "StoreF32S", "f16s": "StoreF16S"}[storage]
         return (f"k_step_f32<{lt},{a},{store}> (tile-map T2C step of Fig. 5: neighbourhood staged per "
                 "block; FP32 collision)")
-    return {"ff_staged": f"k_step_ff<{lt},{a}> (tile-map T2C step of Fig. 5: neighbourhood staged per block; "
-                         "float-float FP64 update)",
+    nt = a ** (3 if lat == 19 else 2)  # nodes per tile
+    staged = (("per-tile neighbour records" if nt <= 64 else "neighbour indices and records") +
+              f" staged per block of {128 if nt <= 256 else nt} nodes")
+    return {"ff_staged": f"k_step_ff<{lt},{a}> (tile-map T2C step of Fig. 5: {staged}; float-float FP64 update)",
             "ff_table_cm": f"k_step_ff_table<{lt}> (per-node gather table built once: the connectivity-matrix "
                            "scheme of Sec. 2.3.1 on compact tiles, not the tile-map method; float-float FP64)",
             "fixed": f"k_step_fixed<{lt},{a}> (tile-map T2C step; 64-bit fixed-point FP64 update)",

@@ -114,8 +114,10 @@ typedef struct lbm_params {
     double f16_scale; /* LBM_STORE_F16S: scale S of the deviations (a power of two
                          keeps the scaling exact); 0 = default 2^16 */
     int block_nodes;  /* fluid nodes per step-kernel block: 0 = default (256, or a^d
-                         when a tile has more nodes); 128 is also compiled for the
-                         FP32 storage forms with 4^3 / 8^2 tiles (autotuner choice) */
+                         when a tile has more nodes; 128 for the LBM_ARITH_FF /
+                         LBM_ARITH_AUTO FP64 step with 4^3 / 8^2 tiles); 128 is
+                         also compiled for the FP32 storage forms with 4^3 / 8^2
+                         tiles (autotuner choice); other values: LBM_ERR_ARG */
     int persistent;   /* 1 = FP32 storage forms run a persistent step kernel: as many
                          blocks as fit on the GPU at once loop over the work list */
     int layout;       /* LBM_LAYOUT_T2C (two PDF copies, default) or LBM_LAYOUT_TGB

@@ -13,17 +13,35 @@ StepLaunch select_step_f64(int lattice, int a, int model, int storage);
 StepLaunch select_step_fixed(int lattice, int a, int model);
 StepLaunch select_step_f32(int lattice, int a, int model, int storage, int block_nodes, int persistent);
 
-StepLaunch select_step_ff(int lattice, int a, int model);
+StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes);
+
+// Fluid nodes per work block of the step kernel: the caller's choice, else
+// 128 for the float-float FP64 step on tiles of at most 128 nodes where a
+// block would hold 256 (six blocks
+// of 128 per SM interleave staging, gather and collision more finely than
+// three of 256: 2-6 % faster, the same bits), else work_threads_for.
+int step_block_nodes(const lbm_params* p) {
+    if (p->block_nodes) return p->block_nodes;
+    const int bd = work_threads_for(p->lattice, p->tile_a);
+    const int nt = p->lattice == LBM_D3Q19 ? p->tile_a * p->tile_a * p->tile_a : p->tile_a * p->tile_a;
+    if (p->layout != LBM_LAYOUT_TGB && p->storage == LBM_STORE_F64 && !p->persistent && bd == 256 && nt <= 128 &&
+        (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO))
+        return 128;  // a work block never splits a tile: only tiles of up to 128 nodes
+    return bd;
+}
 
 StepLaunch select_step(const lbm_params* p) {
     const int lattice = p->lattice, a = p->tile_a, model = p->model, storage = p->storage, arith = p->arith;
     if (storage == LBM_STORE_F64) {
-        if (p->persistent || (p->block_nodes && p->block_nodes != work_threads_for(lattice, a))) return nullptr;
+        if (p->persistent) return nullptr;
+        const bool ff = arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO || arith == LBM_ARITH_FF_TABLE;
+        const int bn = step_block_nodes(p);
+        if (bn != work_threads_for(lattice, a))  // 128-node work blocks: float-float only
+            return ff ? select_step_ff(lattice, a, model, bn) : nullptr;
         StepLaunch f = nullptr;
         if (arith == LBM_ARITH_F64) return select_step_f64(lattice, a, model, storage);
         if (arith == LBM_ARITH_FIXED) f = select_step_fixed(lattice, a, model);
-        if (arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO || arith == LBM_ARITH_FF_TABLE)
-            f = select_step_ff(lattice, a, model);
+        if (ff) f = select_step_ff(lattice, a, model, 0);
         return f ? f : select_step_f64(lattice, a, model, storage);
     }
     return select_step_f32(lattice, a, model, storage, p->block_nodes, p->persistent);
@@ -49,6 +67,7 @@ struct lbm_ctx {
     long long* d_tile_off = nullptr;
     int32_t* d_tile_stride = nullptr;
     ulonglong2* d_tinfo = nullptr;  // packed per-tile record of the step kernels' staging
+    NRec* d_ntab = nullptr;         // per-tile neighbour records of the float-float step (one-word tiles)
     double* d_partials = nullptr;
     double* d_result = nullptr;
     float2* d_u_saved = nullptr;
@@ -147,6 +166,7 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_tile_off);
     cudaFree(c->d_tile_stride);
     cudaFree(c->d_tinfo);
+    cudaFree(c->d_ntab);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_u_saved);
@@ -246,7 +266,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     // work blocks on the host; the fluid-node list they index is written on
     // the device from the tile masks (20 MB for 5 M fluid nodes not copied)
     const long long n_nodes =
-        build_work_list(&T, p->block_nodes ? p->block_nodes : work_threads_for(p->lattice, p->tile_a), 16, false);
+        build_work_list(&T, step_block_nodes(p), 16, false);
     CTRY(cudaMalloc(&c->d_nodes, (size_t)std::max<long long>(n_nodes, 1) * sizeof(uint32_t)));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
@@ -297,6 +317,15 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.tile_off = c->d_tile_off;
     sa.tile_stride = c->d_tile_stride;
     sa.tinfo = c->d_tinfo;
+    // the float-float step on tiles of one mask word stages each neighbourhood
+    // from a per-tile table of neighbour records (16 bytes per slot)
+    if (!c->tgb && T.words == 1 && p->storage == LBM_STORE_F64 &&
+        (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO || p->arith == LBM_ARITH_FF_TABLE) && nf > 0) {
+        const int nn = T.nn;
+        CTRY(cudaMalloc(&c->d_ntab, (size_t)nf * nn * sizeof(NRec)));
+        CTRY(launch_build_ntab(c->d_nbr, c->d_tmask, c->d_tile_off, c->d_tile_stride, nf, nn, c->d_ntab, s));
+        sa.ntab = c->d_ntab;
+    }
     sa.n_tiles = nf;
     sa.n_nodes = n_nodes;
     sa.tau = p->tau;

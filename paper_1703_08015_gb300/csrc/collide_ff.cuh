@@ -180,6 +180,22 @@ __device__ __noinline__ void update_fp64(const NeighShared<Tile<L, A>, KMAX>& sh
     });
 }
 
+// update_fp64 for the steps that stage neighbour records (gather_rec).
+template <class L, int A, int MODEL, int KMAX>
+__device__ __noinline__ void update_fp64_rec(const RecShared<Tile<L, A>, KMAX>& sh, const StepArgs& a,
+                                             const WorkNode& wn, const NodePos<A>& p) {
+    unsigned long long b[L::Q];
+    int stride;
+    unsigned long long* out = gather_rec<L, A, KMAX, unsigned long long>(sh, a.src, a.dst, wn.lt, wn.node, p, b, stride);
+    double f[L::Q];
+    static_for<0, L::Q>([&](auto I) { f[decltype(I)::value] = __longlong_as_double((long long)b[decltype(I)::value]); });
+    collide_f64<L, MODEL>(f, a.omega, a.force);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        out[i * stride] = (unsigned long long)__double_as_longlong(f[i]);
+    });
+}
+
 // ---- two float-float numbers at once (f32x2) ------------------------------------
 // sm_100-family GPUs issue two FP32 additions, multiplications or fused
 // multiply-adds in one instruction (add/sub/mul/fma .f32x2).  The collision

@@ -30,6 +30,16 @@ struct WorkBlock {
     int node_begin, count, tile_begin, n_tiles;
 };
 
+// One neighbour slot of a tile whose fluid nodes fit one mask word (the
+// per-tile neighbourhood table of the float-float step): the neighbour's
+// fluid-node bits, its PDF block relative to the tile's own (values; the
+// tiling keeps every neighbour within 2^30 values), its values per link.
+// All zero for an empty slot.
+struct alignas(16) NRec {
+    unsigned long long m;
+    int off, stride;
+};
+
 // ---- host tiling ------------------------------------------------------------
 // An allocator whose default construction leaves trivial elements as they
 // are: resize() of a vector the tiling then fills completely (in parallel)
@@ -152,6 +162,7 @@ struct StepArgs {
     const long long* tile_off;  // compact layout: PDF block of each tile (in values)
     const int32_t* tile_stride; // compact layout: values per link of each tile
     const ulonglong2* tinfo;    // per tile, one 16-byte record: {first fluid-mask word, tile_off << 24 | tile_stride}
+    const NRec* ntab;           // [n_tiles][3^d] neighbour records (one-word tiles, float-float step) or NULL
     int n_tiles;
     long long n_nodes;          // fluid nodes (entries of the work list)
     const int32_t* gtab;        // FP64 gather table [q + 1][gtab_pitch] (see k_gather_table) or NULL
@@ -219,6 +230,9 @@ NodeLaunch select_export(int lattice, int a, int storage);
 NodeLaunch select_import(int lattice, int a, int storage);
 int node_blocks(int lattice, int a, int n_tiles);  // grid (= partial sums) of the moments kernel
 cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
+// ntab[t][slot] from nbr, tmask (one word per tile), tile_off, tile_stride
+cudaError_t launch_build_ntab(const int32_t* nbr, const uint64_t* tmask, const long long* tile_off,
+                              const int32_t* tile_stride, int n_tiles, int nn, NRec* ntab, cudaStream_t s);
 cudaError_t launch_average(void* cur, const void* prev, size_t bytes, int storage, cudaStream_t s);
 cudaError_t launch_reduce(const double* partials, int nblocks, double* result, cudaStream_t s);
 

@@ -446,6 +446,34 @@ NodeListLaunch select_node_list(int lattice, int a) {
     return nullptr;
 }
 
+// ---- per-tile neighbour records (one-word tiles) -----------------------------------
+__global__ void k_build_ntab(const int32_t* __restrict__ nbr, const uint64_t* __restrict__ tmask,
+                             const long long* __restrict__ tile_off, const int32_t* __restrict__ tile_stride,
+                             int n_tiles, int nn, NRec* __restrict__ ntab) {
+    const long long total = (long long)n_tiles * nn;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(k / nn), nb = nbr[k];
+        NRec r{0ull, 0, 0};
+        if (nb >= 0) {
+            r.m = tmask[nb];
+            r.off = (int)(tile_off[nb] - tile_off[t]);
+            r.stride = tile_stride[nb];
+        }
+        ntab[k] = r;
+    }
+}
+
+cudaError_t launch_build_ntab(const int32_t* nbr, const uint64_t* tmask, const long long* tile_off,
+                              const int32_t* tile_stride, int n_tiles, int nn, NRec* ntab, cudaStream_t s) {
+    const long long total = (long long)n_tiles * nn;
+    if (total == 0) return cudaSuccess;
+    const long long blocks = (total + 255) / 256;
+    k_build_ntab<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(nbr, tmask, tile_off, tile_stride, n_tiles,
+                                                                            nn, ntab);
+    return cudaGetLastError();
+}
+
 // ---- launchers ------------------------------------------------------------------------
 template <class L, int A, int MODEL, class S>
 cudaError_t launch_init(const NodeArgs& a, cudaStream_t s) {

@@ -67,7 +67,7 @@ cudaError_t launch_step_f32(const StepArgs& a, cudaStream_t s) {
 template <class L, int A, int MODEL, class S>
 static StepLaunch pick_shape(int block_nodes, int persistent) {
     constexpr int BD = work_threads<L, A>();
-    if constexpr (BD == 256) {
+    if constexpr (BD == 256 && Tile<L, A>::NT <= 128) {  // a work block never splits a tile
         if (block_nodes == 128)
             return persistent ? &launch_step_f32<L, A, MODEL, S, 128, true> : &launch_step_f32<L, A, MODEL, S, 128, false>;
     }

@@ -24,29 +24,39 @@
 
 namespace lbm {
 
-template <class L, int A, int MODEL, int MINB>
-__global__ void __launch_bounds__(work_threads<L, A>(), MINB) k_step_ff(const StepArgs a) {
+template <class L, int A, int MODEL, int MINB, int BT>
+__global__ void __launch_bounds__(BT, MINB) k_step_ff(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = unsigned long long;
-    __shared__ NeighShared<TL, work_tiles()> sh;
-    WorkNode wn;
-    if (!stage_work<TL, work_tiles(), work_threads<L, A>()>(sh, a, wn)) return;
-    const NodePos<A> p = node_pos<TL>(wn.node);
-    T b[L::Q];
-    const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
-    const int stride = sh.loc[wn.lt][TL::CENTER].y;
-    T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
-    if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) {
+    if constexpr (TL::W == 1) {
+        // the neighbourhood from the per-tile neighbour records
+        __shared__ RecShared<TL, work_tiles()> sh;
+        WorkNode wn;
+        if (!stage_work_rec<TL, work_tiles(), BT>(sh, a, wn)) return;
+        const NodePos<A> p = node_pos<TL>(wn.node);
+        T b[L::Q];
+        int stride;
+        T* out = gather_rec<L, A, work_tiles(), T>(sh, a.src, a.dst, wn.lt, wn.node, p, b, stride);
         // out of range: the same update in native FP64 (a call, so that its
         // registers do not weigh on the float-float path)
-        update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
+        if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) update_fp64_rec<L, A, MODEL, work_tiles()>(sh, a, wn, p);
+    } else {
+        __shared__ NeighShared<TL, work_tiles()> sh;
+        WorkNode wn;
+        if (!stage_work<TL, work_tiles(), BT>(sh, a, wn)) return;
+        const NodePos<A> p = node_pos<TL>(wn.node);
+        T b[L::Q];
+        const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
+        const int stride = sh.loc[wn.lt][TL::CENTER].y;
+        T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
+        if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
     }
 }
 
-template <class L, int A, int MODEL, int MINB>
+template <class L, int A, int MODEL, int MINB, int BT>
 cudaError_t launch_step_ff(const StepArgs& a, cudaStream_t s) {
     if (a.n_work_blocks == 0) return cudaSuccess;
-    k_step_ff<L, A, MODEL, MINB><<<a.n_work_blocks, work_threads<L, A>(), 0, s>>>(a);
+    k_step_ff<L, A, MODEL, MINB, BT><<<a.n_work_blocks, BT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -225,21 +235,33 @@ void ff_consts(const lbm_params* p, FFConsts* k) {
         ff_consts_for<D3Q19>(p, k);
 }
 
-template <class L, int A>
-static StepLaunch pick(int model) {
-    constexpr int MINB = fp64_step_min_blocks<L, A>();
-    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_ff<L, A, LBM_QUASI_COMPRESSIBLE, MINB>
-                                           : &launch_step_ff<L, A, LBM_INCOMPRESSIBLE, MINB>;
+template <class L, int A, int BT>
+static StepLaunch pick_bt(int model) {
+    constexpr int MINB = BT == work_threads<L, A>() ? fp64_step_min_blocks<L, A>() : 768 / BT;
+    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_ff<L, A, LBM_QUASI_COMPRESSIBLE, MINB, BT>
+                                           : &launch_step_ff<L, A, LBM_INCOMPRESSIBLE, MINB, BT>;
 }
 
-StepLaunch select_step_ff(int lattice, int a, int model) {
+// block_nodes: 0 (the default work blocks) or 128 where they hold 256 nodes
+// and a tile fits in 128 (a work block never splits a tile)
+template <class L, int A>
+static StepLaunch pick(int model, int block_nodes) {
+    constexpr int BD = work_threads<L, A>();
+    if constexpr (BD == 256 && Tile<L, A>::NT <= 128) {
+        if (block_nodes == 128) return pick_bt<L, A, 128>(model);
+    }
+    if (block_nodes != 0 && block_nodes != BD) return nullptr;
+    return pick_bt<L, A, BD>(model);
+}
+
+StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes) {
     if (lattice == LBM_D2Q9) {
-        if (a == 8) return pick<D2Q9, 8>(model);
-        if (a == 16) return pick<D2Q9, 16>(model);
-        if (a == 32) return pick<D2Q9, 32>(model);
+        if (a == 8) return pick<D2Q9, 8>(model, block_nodes);
+        if (a == 16) return pick<D2Q9, 16>(model, block_nodes);
+        if (a == 32) return pick<D2Q9, 32>(model, block_nodes);
     } else if (lattice == LBM_D3Q19) {
-        if (a == 4) return pick<D3Q19, 4>(model);
-        if (a == 8) return pick<D3Q19, 8>(model);
+        if (a == 4) return pick<D3Q19, 4>(model, block_nodes);
+        if (a == 8) return pick<D3Q19, 8>(model, block_nodes);
     }
     return nullptr;
 }

@@ -324,4 +324,75 @@ __device__ __forceinline__ bool stage_work(NeighShared<TL, KMAX>& sh, const Step
     return stage_work_at<TL, KMAX, BT>(sh, a, blockIdx.x, wn);
 }
 
+// ---- staging from the per-tile neighbour table (tiles of one mask word) ---------
+// The neighbour records of a work block's tiles lie back to back in the table
+// (NRec, built once at initialisation), so the block copies them with one
+// dependent load instead of two (neighbour index, then that tile's record),
+// as asynchronous 16-byte copies that hold no registers; offsets are relative
+// to each tile's own PDF block.
+template <class TL, int TPB>
+struct RecShared {
+    static_assert(TL::W == 1, "neighbour records hold one mask word");
+    NRec rec[TPB][TL::NN];
+    long long toff[TPB];  // each tile's own PDF block (values)
+};
+
+__device__ __forceinline__ void cp_async16_l2(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8_l1(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class TL, int KMAX, int BT>
+__device__ __forceinline__ bool stage_work_rec(RecShared<TL, KMAX>& sh, const StepArgs& a, WorkNode& wn) {
+    const WorkBlock wb = a.blocks[blockIdx.x];
+    const bool active = (int)threadIdx.x < wb.count;
+    const uint32_t e = active ? __ldg(a.nodes + wb.node_begin + threadIdx.x) : 0u;  // in flight during the copies
+    const int total = wb.n_tiles * TL::NN;
+    const NRec* src = a.ntab + (size_t)wb.tile_begin * TL::NN;
+    for (int k = (int)threadIdx.x; k < total; k += BT) cp_async16_l2(&sh.rec[0][0] + k, src + k);
+    if ((int)threadIdx.x < wb.n_tiles) cp_async8_l1(&sh.toff[threadIdx.x], a.tile_off + wb.tile_begin + threadIdx.x);
+    cp_async_wait_all();
+    __syncthreads();  // the only barrier of the step (Fig. 5)
+    if (!active) return false;
+    wn.tile = (int)(e >> (TL::D * TL::LA));
+    wn.node = (int)(e & (TL::NT - 1));
+    wn.lt = wn.tile - wb.tile_begin;
+    return true;
+}
+
+// gather() from the staged records: the q post-collision words that arrive
+// at `node`; returns the node's values in the copy `dst` and sets its values
+// per link.
+template <class L, int A, int TPB, class T>
+__device__ __forceinline__ T* gather_rec(const RecShared<Tile<L, A>, TPB>& sh, const void* pdf, void* dst, int lt,
+                                         int node, const NodePos<A>& p, T (&f)[L::Q], int& stride) {
+    using TL = Tile<L, A>;
+    const long long toff = sh.toff[lt];
+    const T* org = static_cast<const T*>(pdf) + toff;
+    const NRec own = sh.rec[lt][TL::CENTER];  // offset 0: the tile itself
+    const int own_r = __popcll(own.m & ((1ull << node) - 1ull));
+    f[0] = __ldg(org + own_r);
+    const PullBase<L, A> pb(p);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const PullSource<L, A, i> s(pb);
+        const NRec nb = sh.rec[lt][s.slot];
+        // bit s.sn into the sign bit: the popcount counts the bits at and below it
+        const unsigned long long t = nb.m << (63 - s.sn);
+        const bool fl = (long long)t < 0;
+        const int r = __popcll(t) - (int)fl;
+        const int idx = fl ? nb.off + i * nb.stride + r : own_r + Link<L, i>::opp * own.stride;
+        f[i] = __ldg(org + idx);
+    });
+    stride = own.stride;
+    return static_cast<T*>(dst) + toff + own_r;
+}
+
 }  // namespace lbm

@@ -132,6 +132,27 @@ def test_auto_is_the_staged_float_float_step():
     assert np.array_equal(out[0][:, fl], out[1][:, fl])
 
 
+def test_work_block_size_keeps_the_bits():
+    """The float-float step in work blocks of 128 fluid nodes (the default on
+    4^3 tiles) and of 256 (by request): the same bits.  128-node blocks on
+    tiles of 256 nodes are refused: a work block never splits a tile."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(40, 32, 28), seed=11, r_min=2, r_max=5, target_fluid=0.35)
+    out = []
+    for bn in (0, 128, 256):
+        s = lbm.Solver(mask, 19, 4, (1, 0, 0), 0.6, (1e-5, 0, 0), arith=lbm.LBM_ARITH_FF, block_nodes=bn)
+        try:
+            s.step(40)
+            out.append(s.export_pdfs())
+        finally:
+            s.close()
+    fl = mask.astype(bool)
+    assert np.array_equal(out[0][:, fl], out[1][:, fl]) and np.array_equal(out[0][:, fl], out[2][:, fl])
+    m2, _ = geo.circles_2d(48, 32, seed=3)
+    with pytest.raises(lbm.LBMError):
+        lbm.Solver(m2, 9, 16, (1, 0, 0), 0.8, (1e-6, 0, 0), arith=lbm.LBM_ARITH_FF, block_nodes=128)
+
+
 @pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 def test_moments_and_stats(oracle, arith):
     _cuda()
