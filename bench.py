@@ -188,7 +188,7 @@ class ClockSampler:
 STEP_SOURCES = {  # the sources each step kernel is built from
     "common": ("internal.h", "lattice.cuh", "tile.cuh", "tiling.cpp"),
     "ff_staged": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
-    "ff_table_cm": ("collide_f64.cuh", "collide_ff.cuh", "step_ff.cu"),
+    "ff_table_cm": ("collide_f64.cuh", "collide_ff.cuh", "step_ff_table.cu"),
     "fixed": ("collide_f64.cuh", "step_fixed.cu"),
     "f64": ("collide_f64.cuh", "step_f64.cu"),
     "f32": ("collide_f32.cuh", "step_f32.cu"),
