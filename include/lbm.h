@@ -178,9 +178,12 @@ int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask,
  *              256-byte aligned; they must stay allocated until lbm_free.
  *              With LBM_LAYOUT_TGB, pdf_a is the copy (`pdf_bytes`) and pdf_b
  *              holds the ghost sets (at least lbm_tiling.ghost_bytes).
- *   rho_init   host, dense nx*ny*nz doubles, or NULL for rho0 everywhere.
- *   u_init     host, dense 3 * nx*ny*nz doubles [component][z][y][x], or
- *              NULL for rest.
+ *   rho_init   dense nx*ny*nz doubles, or NULL for rho0 everywhere; device
+ *              memory of the current device is read in place (it must stay
+ *              valid until the fill on `stream` has run), other memory
+ *              (host, another device) is copied first.
+ *   u_init     dense 3 * nx*ny*nz doubles [component][z][y][x] (2 * ... for
+ *              D2Q9), or NULL for rest; memory as for rho_init.
  *   stream     cudaStream_t on which the uploads and the fill run; the call
  *              returns after they have been issued (tables copied from host
  *              memory synchronously).

@@ -59,6 +59,7 @@ struct lbm_ctx {
     int cur = 0;  // copy holding the current post-collision state
     int64_t step = 0;
     int32_t* d_nbr = nullptr;
+    int32_t* d_tile_map = nullptr;  // dense tile map (single geometry, neighbour records built on the device)
     int32_t* d_gtab = nullptr;  // gather table of the FP64 float-float step
     uint64_t* d_tmask = nullptr;
     int32_t* d_coords = nullptr;
@@ -166,6 +167,7 @@ static void release(lbm_ctx* c) {
     cudaFree(c->d_tile_off);
     cudaFree(c->d_tile_stride);
     cudaFree(c->d_tinfo);
+    cudaFree(c->d_tile_map);
     cudaFree(c->d_ntab);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
@@ -260,9 +262,20 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         cudaError_t ce_ = (x);                                    \
         if (ce_ != cudaSuccess) TRY(cuda_fail(ce_, #x));          \
     } while (0)
-    TRY(upload(&c->d_nbr, T.nbr, s));
     TRY(upload(&c->d_tmask, T.tmask, s));
     TRY(upload(&c->d_coords, T.coords, s));
+    const bool device_nbr = T.nbr.empty() && nf > 0;  // tiled without host neighbour records
+    if (device_nbr) {
+        // from the dense tile map (4 B per tile instead of 4 * 3^d B per non-empty tile)
+        TRY(upload(&c->d_tile_map, T.tile_map, s));
+        CTRY(cudaMalloc(&c->d_nbr, (size_t)nf * T.nn * sizeof(int32_t)));
+        const int per[3] = {p->periodic[0] ? 1 : 0, p->periodic[1] ? 1 : 0,
+                            T.d == 3 && p->periodic[2] ? 1 : 0};
+        CTRY(launch_build_nbr(c->d_coords, c->d_tile_map, nf, T.d, T.info.ntx, T.info.nty, T.info.ntz, per,
+                              c->d_nbr, s));
+    } else {
+        TRY(upload(&c->d_nbr, T.nbr, s));
+    }
     // work blocks on the host; the fluid-node list they index is written on
     // the device from the tile masks (20 MB for 5 M fluid nodes not copied)
     const long long n_nodes =
@@ -270,6 +283,19 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     CTRY(cudaMalloc(&c->d_nodes, (size_t)std::max<long long>(n_nodes, 1) * sizeof(uint32_t)));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));
+    if (device_nbr && (long long)c->q * T.info.n_fluid > (1ll << 30)) {
+        // the step kernels address neighbours with 32-bit value offsets
+        unsigned* d_far = nullptr;
+        unsigned far = 0;
+        CTRY(cudaMalloc(&d_far, sizeof(unsigned)));
+        cudaError_t fe = cudaMemsetAsync(d_far, 0, sizeof(unsigned), s);
+        if (fe == cudaSuccess) fe = launch_far_check(c->d_nbr, c->d_tile_off, nf, T.nn, d_far, s);
+        if (fe == cudaSuccess) fe = cudaMemcpyAsync(&far, d_far, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (fe == cudaSuccess) fe = cudaStreamSynchronize(s);
+        cudaFree(d_far);
+        CTRY(fe);
+        if (far) TRY(fail(LBM_ERR_CAPACITY, "neighbour tiles lie more than 2^30 values apart (tile plane too large)"));
+    }
     {
         NodeListLaunch nl = select_node_list(p->lattice, p->tile_a);
         if (!nl) TRY(fail(LBM_ERR_ARG, "no node-list kernel for lattice %d, tile %d", p->lattice, p->tile_a));
@@ -384,18 +410,37 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     // equilibrium start in copy 0; copy 1 is zeroed
     const SampleRange& r0 = samples[0];
     const size_t N0 = (size_t)r0.nx * r0.ny * r0.nz;
-    double* d_rho = nullptr;
-    double* d_u = nullptr;
-    if (rho_init || u_init) {
-        TRY(ensure_stage(c, N0 * 4 * sizeof(double)));
-        if (rho_init) {
-            d_rho = c->d_stage;
-            CTRY(cudaMemcpyAsync(d_rho, rho_init, N0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    // the initial fields: device memory is read in place, host memory staged
+    const double* d_rho = nullptr;
+    const double* d_u = nullptr;
+    bool staged = false;
+    auto on_device = [&](const void* ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
         }
-        if (u_init) {
+        return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device;
+    };
+    if (rho_init) {
+        if (on_device(rho_init)) {
+            d_rho = rho_init;
+        } else {
+            TRY(ensure_stage(c, N0 * 4 * sizeof(double)));
+            CTRY(cudaMemcpyAsync(c->d_stage, rho_init, N0 * sizeof(double), cudaMemcpyDefault, s));
+            d_rho = c->d_stage;
+            staged = true;
+        }
+    }
+    if (u_init) {
+        const size_t nu = (size_t)(p->lattice == LBM_D3Q19 ? 3 : 2) * N0;
+        if (on_device(u_init)) {
+            d_u = u_init;
+        } else {
+            TRY(ensure_stage(c, N0 * 4 * sizeof(double)));
+            CTRY(cudaMemcpyAsync(c->d_stage + N0, u_init, nu * sizeof(double), cudaMemcpyDefault, s));
             d_u = c->d_stage + N0;
-            const size_t nu = (size_t)(p->lattice == LBM_D3Q19 ? 3 : 2) * N0;
-            CTRY(cudaMemcpyAsync(d_u, u_init, nu * sizeof(double), cudaMemcpyHostToDevice, s));
+            staged = true;
         }
     }
     for (size_t k = 0; k < samples.size(); k++) {
@@ -411,7 +456,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         CTRY(init_fn(ia, s));
     }
     CTRY(cudaMemsetAsync(pdf_b, 0, c->tgb ? T.info.ghost_bytes : T.info.pdf_bytes, s));
-    if (rho_init || u_init) CTRY(cudaStreamSynchronize(s));
+    if (staged) CTRY(cudaStreamSynchronize(s));  // the host fields may be released on return
 #undef CTRY
 #undef TRY
     c->cur = 0;
@@ -432,7 +477,7 @@ extern "C" int lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* mask,
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     HostTiling T;
-    int rc = build_tiling(p, mask, &T);
+    int rc = build_tiling(p, mask, &T, false);  // neighbour records built on the device
     if (rc) return rc;
     std::vector<SampleRange> samples{SampleRange{p->nx, p->ny, p->nz, 0, T.info.n_ftiles, T.info.n_fluid}};
     return init_ctx(out, p, T, samples, pdf_a, pdf_b, pdf_bytes, rho_init, u_init, stream);

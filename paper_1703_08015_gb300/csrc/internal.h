@@ -86,7 +86,9 @@ struct SampleRange {
 int build_batch_tiling(const lbm_params* p, int n, const int* dims, const uint8_t* const* masks, HostTiling* T,
                        std::vector<SampleRange>* samples);
 int validate_params(const lbm_params* p);
-int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out);
+// host_nbr false: no neighbour records (T->nbr stays empty) and no check of
+// neighbour distances; the caller builds both on the device (launch_build_nbr)
+int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out, bool host_nbr = true);
 // Step-kernel blocks of at most `threads` nodes and `max_tiles` tiles each,
 // and (want_nodes) the fluid-node list on the host; returns the number of
 // fluid nodes (entries of the list).
@@ -230,6 +232,13 @@ NodeLaunch select_export(int lattice, int a, int storage);
 NodeLaunch select_import(int lattice, int a, int storage);
 int node_blocks(int lattice, int a, int n_tiles);  // grid (= partial sums) of the moments kernel
 cudaError_t launch_fill_nan(double* p, size_t n, cudaStream_t s);
+// the neighbour records of the compact tiles from their coordinates and the
+// dense tile map (build_tiling's rule); a check that no neighbour lies more
+// than 2^30 values away (*far set to 1, else left as it is)
+cudaError_t launch_build_nbr(const int32_t* coords, const int32_t* tile_map, int n_ftiles, int d, int ntx, int nty,
+                             int ntz, const int per[3], int32_t* nbr, cudaStream_t s);
+cudaError_t launch_far_check(const int32_t* nbr, const long long* tile_off, int n_ftiles, int nn, unsigned* far,
+                             cudaStream_t s);
 // ntab[t][slot] from nbr, tmask (one word per tile), tile_off, tile_stride
 cudaError_t launch_build_ntab(const int32_t* nbr, const uint64_t* tmask, const long long* tile_off,
                               const int32_t* tile_stride, int n_tiles, int nn, NRec* ntab, cudaStream_t s);

@@ -446,6 +446,67 @@ NodeListLaunch select_node_list(int lattice, int a) {
     return nullptr;
 }
 
+// ---- neighbour records on the device ------------------------------------------------
+// nbr[k][slot] of compact tile k (coordinates coords[k]) for the 3^d slots
+// (dx fastest, then dy, dz; offsets -1 .. +1): the compact index of the tile at
+// coords + offset, wrapped on a periodic axis, -1 beyond a wall or where the
+// tile was removed -- the host rule of build_tiling.
+__global__ void k_build_nbr(const int32_t* __restrict__ coords, const int32_t* __restrict__ tile_map, int n_ftiles,
+                            int d, int ntx, int nty, int ntz, int perx, int pery, int perz, int32_t* __restrict__ nbr) {
+    const int nn = d == 3 ? 27 : 9;
+    const long long total = (long long)n_ftiles * nn;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / nn), slot = (int)(e - (long long)k * nn);
+        int q[3] = {coords[3 * k] + slot % 3 - 1, coords[3 * k + 1] + (slot / 3) % 3 - 1,
+                    d == 3 ? coords[3 * k + 2] + slot / 9 - 1 : 0};
+        const int nt[3] = {ntx, nty, ntz}, per[3] = {perx, pery, perz};
+        bool ok = true;
+        for (int ax = 0; ax < d; ax++) {
+            if (q[ax] < 0 || q[ax] >= nt[ax]) {
+                if (per[ax])
+                    q[ax] = (q[ax] + nt[ax]) % nt[ax];
+                else
+                    ok = false;
+            }
+        }
+        nbr[e] = ok ? tile_map[((long long)q[2] * nty + q[1]) * ntx + q[0]] : -1;
+    }
+}
+
+// *far = 1 if a tile and one of its neighbours lie more than 2^30 values apart
+__global__ void k_far_check(const int32_t* __restrict__ nbr, const long long* __restrict__ tile_off, int n_ftiles,
+                            int nn, unsigned* far) {
+    const long long total = (long long)n_ftiles * nn;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int nb = nbr[e];
+        if (nb >= 0) {
+            const long long dv = tile_off[nb] - tile_off[e / nn];
+            if (dv > (1ll << 30) || dv < -(1ll << 30)) atomicOr(far, 1u);
+        }
+    }
+}
+
+cudaError_t launch_build_nbr(const int32_t* coords, const int32_t* tile_map, int n_ftiles, int d, int ntx, int nty,
+                             int ntz, const int per[3], int32_t* nbr, cudaStream_t s) {
+    const long long total = (long long)n_ftiles * (d == 3 ? 27 : 9);
+    if (total == 0) return cudaSuccess;
+    const long long blocks = (total + 255) / 256;
+    k_build_nbr<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(coords, tile_map, n_ftiles, d, ntx, nty, ntz,
+                                                                         per[0], per[1], per[2], nbr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_check(const int32_t* nbr, const long long* tile_off, int n_ftiles, int nn, unsigned* far,
+                             cudaStream_t s) {
+    const long long total = (long long)n_ftiles * nn;
+    if (total == 0) return cudaSuccess;
+    const long long blocks = (total + 255) / 256;
+    k_far_check<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(nbr, tile_off, n_ftiles, nn, far);
+    return cudaGetLastError();
+}
+
 // ---- per-tile neighbour records (one-word tiles) -----------------------------------
 __global__ void k_build_ntab(const int32_t* __restrict__ nbr, const uint64_t* __restrict__ tmask,
                              const long long* __restrict__ tile_off, const int32_t* __restrict__ tile_stride,

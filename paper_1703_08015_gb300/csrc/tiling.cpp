@@ -11,41 +11,104 @@
 // PDFs are stored compactly: a tile's block holds only its fluid nodes (in
 // row order), so solid nodes of porous tiles cost neither memory nor
 // bandwidth; a node's slot is its rank among the tile's fluid nodes.
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <thread>
 
 #include "internal.h"
 
 namespace lbm {
 
+// Host threads for the tiling, started once per process (the calling
+// thread takes a share too): starting threads for every parallel pass cost
+// about 0.4 ms per pass on the Grace host, more than most passes' work.  The
+// workers sleep on a condition variable between calls; one call uses the pool
+// at a time (a concurrent call runs serially), and a forked child, which has
+// no copy of the workers, starts its own pool.
+struct HostPool {
+    std::mutex mu, busy;
+    std::condition_variable work_cv, done_cv;
+    const std::function<void(int64_t, int64_t)>* job = nullptr;
+    int64_t n = 0, chunk = 0;
+    int n_chunks = 0, next = 0, remaining = 0;
+    int threads = 1;  // workers + the caller
+    pid_t pid = 0;
+
+    // take chunks until none is left; returns with `lk` held
+    void run_chunks(std::unique_lock<std::mutex>& lk) {
+        while (next < n_chunks) {
+            const int c = next++;
+            const int64_t b = (int64_t)c * chunk, e = std::min(n, b + chunk);
+            lk.unlock();
+            (*job)(b, e);
+            lk.lock();
+            if (--remaining == 0) done_cv.notify_all();
+        }
+    }
+    void worker() {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            work_cv.wait(lk, [&] { return next < n_chunks; });
+            run_chunks(lk);
+        }
+    }
+};
+
+static HostPool* host_pool() {
+    static std::mutex init;
+    static HostPool* pool = nullptr;
+    std::lock_guard<std::mutex> g(init);
+    if (pool && pool->pid == getpid()) return pool;
+    // first use, or a forked child: a new pool (a parent's is left as it is)
+    HostPool* p = new HostPool();
+    p->pid = getpid();
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int want = (int)std::max(1u, std::min(hc ? hc : 1u, 16u));
+    for (int k = 1; k < want; k++) {
+        try {
+            std::thread(&HostPool::worker, p).detach();
+            p->threads++;
+        } catch (...) {
+            break;
+        }
+    }
+    pool = p;
+    return pool;
+}
+
 // f(begin, end) over [0, n) in up to 16 host threads (each range a contiguous
 // block of items; the caller's results depend only on the item, not on the
-// split).  Runs serially for small n or when threads cannot be started.
+// split).  Runs serially for small n or while another call holds the pool.
 template <class F>
 static void parallel_ranges(int64_t n, int64_t min_per_thread, F f) {
-    const unsigned hc = std::thread::hardware_concurrency();
-    int64_t t = std::min<int64_t>(hc ? std::min(hc, 16u) : 1u, n / std::max<int64_t>(min_per_thread, 1));
-    if (t <= 1) {
+    HostPool* P = host_pool();
+    const int64_t t = std::min<int64_t>(P->threads, n / std::max<int64_t>(min_per_thread, 1));
+    std::unique_lock<std::mutex> busy(P->busy, std::try_to_lock);
+    if (t <= 1 || !busy.owns_lock()) {
         f((int64_t)0, n);
         return;
     }
-    const int64_t chunk = (n + t - 1) / t;
-    std::vector<std::thread> pool;
-    int64_t done = 0;  // items handed to started threads
-    try {
-        for (int64_t b = 0; b < n; b += chunk) {
-            pool.emplace_back(f, b, std::min(n, b + chunk));
-            done = std::min(n, b + chunk);
-        }
-    } catch (...) {
-    }
-    for (auto& th : pool) th.join();
-    if (done < n) f(done, n);  // threads could not be started: finish here
+    const std::function<void(int64_t, int64_t)> job = f;
+    std::unique_lock<std::mutex> lk(P->mu);
+    P->job = &job;
+    P->n = n;
+    P->chunk = (n + t - 1) / t;
+    P->n_chunks = (int)((n + P->chunk - 1) / P->chunk);
+    P->next = 0;
+    P->remaining = P->n_chunks;
+    P->work_cv.notify_all();
+    P->run_chunks(lk);
+    P->done_cv.wait(lk, [&] { return P->remaining == 0; });
+    P->job = nullptr;
 }
 
 static thread_local char g_err[512] = "";
@@ -104,7 +167,7 @@ int validate_params(const lbm_params* p) {
     return LBM_OK;
 }
 
-int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
+int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T, bool host_nbr) {
     int rc = validate_params(p);
     if (rc) return rc;
     if (!mask) return fail(LBM_ERR_ARG, "mask is NULL");
@@ -223,44 +286,47 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
 
     // neighbour records through a tile map padded by one tile on each side:
     // the pad holds the wrapped tile on a periodic axis, -1 beyond a wall
+    // (without host_nbr the caller builds them on the device from tile_map)
     const int per[3] = {p->periodic[0] ? 1 : 0, p->periodic[1] ? 1 : 0, d == 3 && p->periodic[2] ? 1 : 0};
-    const int ntv[3] = {ntx, nty, ntz};
-    const int px = ntx + 2, py = nty + 2, pz = d == 3 ? ntz + 2 : 1;
-    std::vector<int32_t> pmap((size_t)px * py * pz, -1);
-    parallel_ranges(pz, 4, [&](int64_t z0, int64_t z1) {
-        for (int64_t zz = z0; zz < z1; zz++)
-            for (int yy = 0; yy < py; yy++)
-                for (int xx = 0; xx < px; xx++) {
-                    int q[3] = {xx - 1, yy - 1, d == 3 ? (int)zz - 1 : 0};
-                    bool ok = true;
-                    for (int ax = 0; ax < d; ax++) {
-                        if (q[ax] < 0 || q[ax] >= ntv[ax]) {
-                            if (per[ax])
-                                q[ax] = (q[ax] + ntv[ax]) % ntv[ax];
-                            else
-                                ok = false;
+    if (host_nbr) {
+        const int ntv[3] = {ntx, nty, ntz};
+        const int px = ntx + 2, py = nty + 2, pz = d == 3 ? ntz + 2 : 1;
+        std::vector<int32_t> pmap((size_t)px * py * pz, -1);
+        parallel_ranges(pz, 4, [&](int64_t z0, int64_t z1) {
+            for (int64_t zz = z0; zz < z1; zz++)
+                for (int yy = 0; yy < py; yy++)
+                    for (int xx = 0; xx < px; xx++) {
+                        int q[3] = {xx - 1, yy - 1, d == 3 ? (int)zz - 1 : 0};
+                        bool ok = true;
+                        for (int ax = 0; ax < d; ax++) {
+                            if (q[ax] < 0 || q[ax] >= ntv[ax]) {
+                                if (per[ax])
+                                    q[ax] = (q[ax] + ntv[ax]) % ntv[ax];
+                                else
+                                    ok = false;
+                            }
                         }
+                        pmap[((size_t)zz * py + yy) * px + xx] =
+                            ok ? T->tile_map[((size_t)q[2] * nty + q[1]) * ntx + q[0]] : -1;
                     }
-                    pmap[((size_t)zz * py + yy) * px + xx] =
-                        ok ? T->tile_map[((size_t)q[2] * nty + q[1]) * ntx + q[0]] : -1;
-                }
-    });
-    int64_t off[27];
-    {
-        int slot = 0;
-        for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++, slot++) off[slot] = ((int64_t)dz * py + dy) * px + dx;
-    }
-    T->nbr.resize((size_t)count * T->nn);
-    parallel_ranges(count, 1024, [&](int64_t k0, int64_t k1) {
-        for (int64_t k = k0; k < k1; k++) {
-            const int* c = &T->coords[(size_t)3 * k];
-            const int64_t centre = ((int64_t)(d == 3 ? c[2] + 1 : 0) * py + (c[1] + 1)) * px + (c[0] + 1);
-            int32_t* out = &T->nbr[(size_t)k * T->nn];
-            for (int slot = 0; slot < T->nn; slot++) out[slot] = pmap[(size_t)(centre + off[slot])];
+        });
+        int64_t off[27];
+        {
+            int slot = 0;
+            for (int dz = (d == 3 ? -1 : 0); dz <= (d == 3 ? 1 : 0); dz++)
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++, slot++) off[slot] = ((int64_t)dz * py + dy) * px + dx;
         }
-    });
+        T->nbr.resize((size_t)count * T->nn);
+        parallel_ranges(count, 1024, [&](int64_t k0, int64_t k1) {
+            for (int64_t k = k0; k < k1; k++) {
+                const int* c = &T->coords[(size_t)3 * k];
+                const int64_t centre = ((int64_t)(d == 3 ? c[2] + 1 : 0) * py + (c[1] + 1)) * px + (c[0] + 1);
+                int32_t* out = &T->nbr[(size_t)k * T->nn];
+                for (int slot = 0; slot < T->nn; slot++) out[slot] = pmap[(size_t)(centre + off[slot])];
+            }
+        });
+    }
 
     // Compact layout: a tile stores only its fluid nodes, in row order, link
     // after link with no padding (contiguous link arrays fill whole sectors).
@@ -292,7 +358,7 @@ int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* T) {
     // from the first tile of their block: neighbours must lie within 2^30
     // values (always so when the whole copy holds fewer values)
     std::atomic<bool> far{false};
-    if (total > (1ll << 30)) parallel_ranges(count, 4096, [&](int64_t k0, int64_t k1) {
+    if (host_nbr && total > (1ll << 30)) parallel_ranges(count, 4096, [&](int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1 && !far.load(std::memory_order_relaxed); k++)
             for (int slot = 0; slot < T->nn; slot++) {
                 const int32_t nb = T->nbr[(size_t)k * T->nn + slot];
@@ -383,11 +449,17 @@ long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_n
     T->nodes.clear();
     T->blocks.clear();
     // first node of every tile (a prefix count), then the block boundaries
+    // (a tile's stride is its fluid count: the compact layout has no padding)
+    const bool have_counts = T->tile_stride.size() == (size_t)n;
     std::vector<int64_t> first((size_t)n + 1, 0);
     for (int32_t k = 0; k < n; k++) {
-        const uint64_t* m = &T->tmask[(size_t)k * T->words];
         int nf = 0;
-        for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(m[w]);
+        if (have_counts) {
+            nf = T->tile_stride[k];
+        } else {
+            const uint64_t* m = &T->tmask[(size_t)k * T->words];
+            for (int w = 0; w < T->words; w++) nf += __builtin_popcountll(m[w]);
+        }
         first[k + 1] = first[k] + nf;
     }
     WorkBlock cur{0, 0, 0, 0};

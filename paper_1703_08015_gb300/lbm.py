@@ -158,11 +158,22 @@ def lbm_init(params: lbm_params, mask, pdf_a, pdf_b, pdf_bytes, rho_init=None, u
     lib = library()
     ctx = ctypes.c_void_p()
     m = np.ascontiguousarray(mask, np.uint8)
-    r = None if rho_init is None else np.ascontiguousarray(rho_init, np.float64)
-    u = None if u_init is None else np.ascontiguousarray(u_init, np.float64)
+    r, u = _field(rho_init), _field(u_init)
     _check(lib.lbm_init(ctypes.byref(ctx), ctypes.byref(params), _ptr(m), _ptr(pdf_a), _ptr(pdf_b),
                         pdf_bytes, _ptr(r), _ptr(u), stream))
     return ctx
+
+
+def _field(x):
+    """An initial field as a contiguous FP64 array: device tensors stay on the
+    device (lbm_init reads them in place), anything else goes through numpy."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        import torch
+
+        return x.detach().to(torch.float64).contiguous()
+    return np.ascontiguousarray(x, np.float64)
 
 
 def lbm_step(ctx, nsteps, stream=None):

@@ -621,9 +621,10 @@ def train(net, masks_dev, fields, force, nu, epochs=20, batch=8, lr=2e-3, lr_min
     return hist
 
 
-def predict_fields(net, mask, force, nu):
-    """Warm-start (rho[nz][ny][nx], u[3][nz][ny][nx]) FP64 host arrays for one
-    geometry, computed on the device by the network."""
+def predict_fields(net, mask, force, nu, on_device=False):
+    """Warm-start (rho[nz][ny][nx], u[3][nz][ny][nx]) FP64 fields for one
+    geometry, computed on the device by the network: host arrays, or with
+    on_device the device tensors (lbm_init reads them in place)."""
     torch = net.torch
     m = torch.from_numpy(np.ascontiguousarray(mask, np.uint8)).to(net.device)[None]
     x = inputs_from_masks(m, force, net._s())
@@ -634,6 +635,9 @@ def predict_fields(net, mask, force, nu):
     u = torch.empty(3 * vox, dtype=torch.float64, device=net.device)
     lbm_nn_target_to_fields(y, vox, 1.0, net.meta["a_rho"] * force, net.meta["a_u"] * force / nu, rho, u,
                             net._s())
+    if on_device:  # work queued on the current stream after this sees the fields
+        torch.cuda.current_stream(net.device).wait_stream(net.stream)
+        return rho.view(tuple(mask.shape)), u.view((3,) + tuple(mask.shape))
     return rho.cpu().numpy().reshape(mask.shape), u.cpu().numpy().reshape((3,) + tuple(mask.shape))
 
 
@@ -658,7 +662,7 @@ def time_to_steady(mask, net=None, tau=0.6, force=1e-6, storage=lbm.LBM_STORE_F6
     t0 = time.perf_counter()
     rho0 = u0 = None
     if net is not None:
-        rho0, u0 = predict_fields(net, mask, force, nu)
+        rho0, u0 = predict_fields(net, mask, force, nu, on_device=True)
     s = lbm.Solver(mask, lbm.LBM_D3Q19, 4, (1, 0, 0), tau, (force, 0, 0), storage=storage, rho_init=rho0,
                    u_init=u0, device=dev)
     s.stats(residual=True)
