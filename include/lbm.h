@@ -163,9 +163,11 @@ typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library */
  *   out       host out, the counts and the bytes of one PDF copy.
  * The mask scan and the neighbour records run over tile rows in up to 16
  * host threads (the result does not depend on their number); lbm_init tiles
- * the same way.
+ * the same way and builds the same neighbour records on the device.
  * Errors: LBM_ERR_ARG (NULL mask/out/p, bad sizes or tile edge),
- * LBM_ERR_SHAPE (periodic axis not a multiple of tile_a). */
+ * LBM_ERR_SHAPE (periodic axis not a multiple of tile_a), LBM_ERR_CAPACITY
+ * (too many tiles; with nbr given, neighbours more than 2^30 values apart,
+ * which lbm_init reports in any case). */
 int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask,
                       int32_t* tile_map, int32_t* nbr, lbm_tiling* out);
 

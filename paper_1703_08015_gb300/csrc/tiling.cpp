@@ -498,7 +498,7 @@ extern "C" int lbm_build_tilemap(const lbm_params* p, const uint8_t* mask, int32
     using namespace lbm;
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     HostTiling T;
-    int rc = build_tiling(p, mask, &T);
+    int rc = build_tiling(p, mask, &T, nbr != nullptr);  // a size query skips the neighbour records
     if (rc) return rc;
     *out = T.info;
     if (tile_map) std::memcpy(tile_map, T.tile_map.data(), T.tile_map.size() * sizeof(int32_t));
