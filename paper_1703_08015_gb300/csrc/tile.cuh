@@ -238,10 +238,12 @@ struct WorkNode {
 
 // Resident blocks per SM the float-float and fixed-point FP64 steps ask the
 // compiler to allow (it caps their registers): three blocks of 256 threads
-// (80 registers; two blocks measured slower), one block of more threads.
+// (80 registers; two blocks measured slower), two of 512 (64 registers: the
+// 8^3-tile D3Q19 step spills 168 B but runs at 644 against 909 us per 256^3
+// step with one block of 128 registers).
 template <class L, int A>
 constexpr int fp64_step_min_blocks() {
-    return work_threads<L, A>() <= 256 ? 3 : 1;
+    return work_threads<L, A>() <= 256 ? 3 : (work_threads<L, A>() <= 512 ? 2 : 1);
 }
 
 // The block's BT threads copy the neighbourhoods of work block `wb`'s tiles
