@@ -343,15 +343,6 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     sa.tile_off = c->d_tile_off;
     sa.tile_stride = c->d_tile_stride;
     sa.tinfo = c->d_tinfo;
-    // the float-float step on tiles of one mask word stages each neighbourhood
-    // from a per-tile table of neighbour records (16 bytes per slot)
-    if (!c->tgb && T.words == 1 && p->storage == LBM_STORE_F64 &&
-        (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO || p->arith == LBM_ARITH_FF_TABLE) && nf > 0) {
-        const int nn = T.nn;
-        CTRY(cudaMalloc(&c->d_ntab, (size_t)nf * nn * sizeof(NRec)));
-        CTRY(launch_build_ntab(c->d_nbr, c->d_tmask, c->d_tile_off, c->d_tile_stride, nf, nn, c->d_ntab, s));
-        sa.ntab = c->d_ntab;
-    }
     sa.n_tiles = nf;
     sa.n_nodes = n_nodes;
     sa.tau = p->tau;
@@ -386,6 +377,15 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         } else if (ae == cudaErrorMemoryAllocation) {
             (void)cudaGetLastError();  // no room for the table: the staged step needs none
         }
+    }
+    // the staged float-float step on tiles of one mask word reads each
+    // neighbourhood from a per-tile table of neighbour records (16 B per slot)
+    if (!c->tgb && !sa.gtab && T.words == 1 && p->storage == LBM_STORE_F64 &&
+        (p->arith == LBM_ARITH_FF || p->arith == LBM_ARITH_AUTO || p->arith == LBM_ARITH_FF_TABLE) && nf > 0) {
+        const int nn = T.nn;
+        CTRY(cudaMalloc(&c->d_ntab, (size_t)nf * nn * sizeof(NRec)));
+        CTRY(launch_build_ntab(c->d_nbr, c->d_tmask, c->d_tile_off, c->d_tile_stride, nf, nn, c->d_ntab, s));
+        sa.ntab = c->d_ntab;
     }
 
     NodeArgs& na = c->na;  // a launch over every tile; sample launches narrow it
