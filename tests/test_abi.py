@@ -70,6 +70,61 @@ def test_tilemap_workload_sphere_pack():
     _check_tiling(mask, lbm.LBM_D3Q19, 4, (1, 0, 0))
 
 
+def _tiling_of(mask, a=4, per=(1, 0, 0)):
+    p = lbm.make_params(lbm.LBM_D3Q19, mask.shape, a, per)
+    info, tm, nb = lbm.lbm_build_tilemap(p, mask)
+    return int(info.n_ftiles), int(info.pdf_bytes), tm, nb
+
+
+def test_tiling_from_several_threads_at_once():
+    """The host tiling runs its passes on a pool of threads started once; calls
+    from several threads at once (one gets the pool, the others run serially)
+    give the same tables as one call at a time."""
+    import threading
+
+    masks = [geo.sphere_pack_3d(shape=(48, 40, 32), seed=s, r_min=2, r_max=6)[0] for s in range(6)]
+    want = [_tiling_of(m) for m in masks]
+    got = [None] * len(masks)
+
+    def run(k):
+        for _ in range(3):
+            got[k] = _tiling_of(masks[k])
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(len(masks))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for w, g in zip(want, got):
+        assert w[:2] == g[:2] and np.array_equal(w[2], g[2]) and np.array_equal(w[3], g[3])
+
+
+def _tile_in_child(q):
+    m = geo.sphere_pack_3d(shape=(32, 32, 32), seed=4, r_min=2, r_max=5)[0]
+    q.put(_tiling_of(m)[:2])
+
+
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded:DeprecationWarning")
+def test_tiling_in_a_forked_child():
+    """A child forked after the pool has started has none of its threads: it
+    starts its own pool and tiles to the same result (no hang)."""
+    import multiprocessing as mp
+
+    m = geo.sphere_pack_3d(shape=(32, 32, 32), seed=4, r_min=2, r_max=5)[0]
+    want = _tiling_of(m)[:2]  # the parent's pool is running
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_tile_in_child, args=(q,))
+    pr.start()
+    pr.join(60)
+    if pr.is_alive():
+        pr.kill()
+        pr.join()
+        pytest.fail("tiling in a forked child did not finish")
+    assert pr.exitcode == 0
+    assert q.get(timeout=5) == want
+
+
 def test_tilemap_edge_cases():
     z = np.zeros((8, 8, 8), np.uint8)
     p = lbm.make_params(lbm.LBM_D3Q19, z.shape, 4)
