@@ -279,7 +279,7 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
     // work blocks on the host; the fluid-node list they index is written on
     // the device from the tile masks (20 MB for 5 M fluid nodes not copied)
     const long long n_nodes =
-        build_work_list(&T, step_block_nodes(p), 16, false);
+        build_work_list(&T, step_block_nodes(p), 16, false, !c->tgb);
     CTRY(cudaMalloc(&c->d_nodes, (size_t)std::max<long long>(n_nodes, 1) * sizeof(uint32_t)));
     TRY(upload(&c->d_blocks, T.blocks, s));
     TRY(upload(&c->d_tile_off, T.tile_off, s));

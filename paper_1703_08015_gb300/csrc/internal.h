@@ -91,8 +91,11 @@ int validate_params(const lbm_params* p);
 int build_tiling(const lbm_params* p, const uint8_t* mask, HostTiling* out, bool host_nbr = true);
 // Step-kernel blocks of at most `threads` nodes and `max_tiles` tiles each,
 // and (want_nodes) the fluid-node list on the host; returns the number of
-// fluid nodes (entries of the list).
-long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes = true);
+// fluid nodes (entries of the list).  With split_tiles a tile's nodes may be
+// shared by two consecutive blocks, so that every block but the last holds
+// `threads` nodes (only for steps that read one copy and write the other:
+// the in-place ghost-buffer step updates a tile from one block).
+long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes = true, bool split_tiles = false);
 int work_threads_for(int lattice, int a);
 int lattice_q(int lattice);
 size_t bytes_per_value(int storage);

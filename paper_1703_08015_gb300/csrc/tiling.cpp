@@ -443,7 +443,7 @@ int work_threads_for(int lattice, int a) {
 
 // Fluid nodes in tile-major, row order, cut into blocks of consecutive tiles
 // holding at most `threads` nodes and `max_tiles` tiles.
-long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes) {
+long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_nodes, bool split_tiles) {
     const int nt = T->d == 3 ? T->a * T->a * T->a : T->a * T->a;
     const int32_t n = T->info.n_ftiles;
     T->nodes.clear();
@@ -463,18 +463,44 @@ long long build_work_list(HostTiling* T, int threads, int max_tiles, bool want_n
         first[k + 1] = first[k] + nf;
     }
     WorkBlock cur{0, 0, 0, 0};
-    for (int32_t k = 0; k < n; k++) {
-        const int nf = (int)(first[k + 1] - first[k]);
-        if (cur.n_tiles > 0 && (cur.count + nf > threads || cur.n_tiles == max_tiles)) {
-            T->blocks.push_back(cur);
-            cur = WorkBlock{0, 0, 0, 0};
+    if (split_tiles) {
+        // every block full (`threads` nodes) but the last: a tile that does not
+        // fit continues in the next block (the list holds a tile's nodes in a row)
+        for (int32_t k = 0; k < n; k++) {
+            int64_t at = first[k];
+            while (at < first[k + 1]) {
+                if (cur.n_tiles == max_tiles) {
+                    T->blocks.push_back(cur);
+                    cur = WorkBlock{0, 0, 0, 0};
+                }
+                if (cur.n_tiles == 0) {
+                    cur.node_begin = (int)at;
+                    cur.tile_begin = k;
+                }
+                const int take = (int)std::min<int64_t>(first[k + 1] - at, threads - cur.count);
+                cur.count += take;
+                cur.n_tiles++;
+                at += take;
+                if (cur.count == threads) {
+                    T->blocks.push_back(cur);
+                    cur = WorkBlock{0, 0, 0, 0};
+                }
+            }
         }
-        if (cur.n_tiles == 0) {
-            cur.node_begin = (int)first[k];
-            cur.tile_begin = k;
+    } else {
+        for (int32_t k = 0; k < n; k++) {
+            const int nf = (int)(first[k + 1] - first[k]);
+            if (cur.n_tiles > 0 && (cur.count + nf > threads || cur.n_tiles == max_tiles)) {
+                T->blocks.push_back(cur);
+                cur = WorkBlock{0, 0, 0, 0};
+            }
+            if (cur.n_tiles == 0) {
+                cur.node_begin = (int)first[k];
+                cur.tile_begin = k;
+            }
+            cur.count += nf;
+            cur.n_tiles++;
         }
-        cur.count += nf;
-        cur.n_tiles++;
     }
     if (cur.n_tiles > 0) T->blocks.push_back(cur);
     if (!want_nodes) return first[n];
