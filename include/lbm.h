@@ -122,6 +122,12 @@ typedef struct lbm_params {
                          blocks as fit on the GPU at once loop over the work list */
     int layout;       /* LBM_LAYOUT_T2C (two PDF copies, default) or LBM_LAYOUT_TGB
                          (one copy updated in place plus ghost buffers, Sec. 3.1) */
+    int prefetch_blocks; /* LBM_LAYOUT_T2C (not in the paper): each block of the step
+                         kernel asks the L2 for the source values of the work block
+                         this many blocks ahead, so that its gathers find them there
+                         (the FP32 storage forms also for that block's node list and
+                         neighbour indices); 0 = default (4 per SM), < 0 = off.
+                         Timing only: results do not depend on it */
 } lbm_params;
 
 typedef struct lbm_tiling {

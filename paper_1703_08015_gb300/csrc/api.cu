@@ -387,6 +387,20 @@ static int init_ctx(lbm_ctx** out, const lbm_params* p, HostTiling& T, const std
         CTRY(launch_build_ntab(c->d_nbr, c->d_tmask, c->d_tile_off, c->d_tile_stride, nf, nn, c->d_ntab, s));
         sa.ntab = c->d_ntab;
     }
+    sa.pf_node_bytes = (int)(bytes_per_value(p->storage) * (size_t)lattice_q(p->lattice));
+    sa.pf_limit = (long long)(T.info.pdf_bytes & ~(size_t)15);
+    {
+        // L2 prefetch distance: about 0.6 of the FP64 step's resident blocks
+        // (seven per SM), 0.7 of the FP32 forms' (six per SM); further ahead
+        // the prefetched lines start to evict the ones still being read
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
+        sa.pf_ahead = p->prefetch_blocks < 0 ? 0 : (p->prefetch_blocks > 0 ? p->prefetch_blocks : 4 * sms);
+        if (sa.pf_ahead > sa.n_work_blocks) sa.pf_ahead = sa.n_work_blocks;
+        // the FP32 forms stage through neighbour indices (two dependent loads):
+        // their tables gain from the prefetch, the FP64 records did not
+        sa.pf_tables = p->storage != LBM_STORE_F64;
+    }
 
     NodeArgs& na = c->na;  // a launch over every tile; sample launches narrow it
     na.nbr = c->d_nbr;

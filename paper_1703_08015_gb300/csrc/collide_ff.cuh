@@ -121,26 +121,31 @@ __device__ __forceinline__ ff q60_to_ff(long long x) {
 }
 
 // a + b + c with the rounding errors of both high-part sums kept in the low
-// part (not renormalised: ulp_round takes any low part below 2^30).
+// part (not renormalised: ulp_round takes any low part below 1.5 2^24).
 __device__ __forceinline__ ff ff_sum3(ff a, ff b, ff c) {
     const ff s = two_sum(a.h, b.h);
     const ff t = two_sum(s.h, c.h);
     return ff{t.h, __fadd_rn(__fadd_rn(__fadd_rn(a.l, b.l), __fadd_rn(c.l, s.l)), t.l)};
 }
 
-// FP64 bit pattern of w + r ulp(w) with r = RN(x.h) + RN(x.l), within one unit
-// of x = x.h + x.l (units of ulp(w)).  x.h is split at 2^24 by rounding it to
-// the nearest multiple of 2^24 with one addition: t = x.h + 1.5 2^47 lies in
-// [2^47, 2^48) for |x.h| < 2^46, where the floats are the multiples of 2^24, so
-// bits(t) - bits(1.5 2^47) counts them and the remainder x.h - (t - 1.5 2^47)
-// is exact (|rem| <= 2^23).  Subtracting an even integer commutes with
-// round-to-nearest-even, so RN(rem) + (t - 1.5 2^47) = RN(x.h).  (Three FP32
-// <-> int conversions per value, as a truncating split would take, issue at
-// a fraction of the FP32 rate.)
+// FP64 bit pattern of w + r ulp(w) with r within one unit of x = x.h + x.l
+// (units of ulp(w)).  x.h is split at 2^24 by rounding it to the nearest
+// multiple of 2^24 with one addition: t = x.h + 1.5 2^47 lies in [2^47, 2^48)
+// for |x.h| < 2^46, where the floats are the multiples of 2^24, so
+// bits(t) - bits(1.5 2^47) counts them and the remainder rem = x.h - (t -
+// 1.5 2^47) is exact (|rem| <= 2^23).  With |x.l| < 1.5 2^24 (the low part of
+// keep d_i alone reaches 2^24 near equilibrium: d_i's low piece is not
+// centred), |rem + x.l| < 2^25: below 2^24 its float sum and the conversion to
+// an integer are each within 1/2, at or above 2^24 the sum is already an
+// integer within 1; so r = (t - 1.5 2^47) + RN_int(rem + x.l) is within one
+// unit of x.  (A truncating split would take three FP32 <-> int conversions
+// per value, which issue at a fraction of the FP32 rate; one conversion of the
+// summed remainder instead of one per part measured 1 % faster.)
 //
 // The result stays in the binade of w (same sign and exponent bits): |r| <
-// 2^46 + 2^30 + 1 ulps, and every lattice weight lies at least 2^48 ulps from
+// 2^46 + 2^26 ulps, and every lattice weight lies at least 2^48 ulps from
 // the edges of its binade (checked at compile time in collide_ff).
+constexpr float kLowBound = 25165824.0f;  // 1.5 * 2^24
 constexpr float kSplit24 = 211106232532992.0f;  // 1.5 * 2^47: floats in [2^47, 2^48) are multiples of 2^24
 __device__ __forceinline__ unsigned long long ulp_assemble(unsigned long long wb, float t, int lo) {
     const long long k = (long long)wb - ((long long)__float_as_int(kSplit24) << 24);
@@ -148,10 +153,10 @@ __device__ __forceinline__ unsigned long long ulp_assemble(unsigned long long wb
 }
 
 __device__ __forceinline__ unsigned long long ulp_round(ff x, unsigned long long wb, bool& ok) {
-    ok &= fabsf(x.h) < pow2f(46) && fabsf(x.l) < pow2f(30);
+    ok &= fabsf(x.h) < pow2f(46) && fabsf(x.l) < kLowBound;
     const float t = __fadd_rn(x.h, kSplit24);
     const float rem = __fsub_rn(x.h, __fsub_rn(t, kSplit24));  // exact, |rem| <= 2^23
-    return ulp_assemble(wb, t, __float2int_rn(rem) + __float2int_rn(x.l));
+    return ulp_assemble(wb, t, __float2int_rn(__fadd_rn(rem, x.l)));  // |rem + x.l| < 2^25
 }
 
 template <class L, int C>
@@ -298,12 +303,13 @@ __device__ __forceinline__ ff2 d_to_ff_2(long long a, long long b) {
 // ulp_round of two results (bit patterns of two links of weight bits wa, wb).
 __device__ __forceinline__ void ulp_round_2(ff2 x, unsigned long long wa, unsigned long long wb, bool& ok,
                                             unsigned long long& oa, unsigned long long& ob) {
-    ok &= fabsf(x.h.x) < pow2f(46) && fabsf(x.l.x) < pow2f(30) && fabsf(x.h.y) < pow2f(46) &&
-          fabsf(x.l.y) < pow2f(30);
+    ok &= fabsf(x.h.x) < pow2f(46) && fabsf(x.l.x) < kLowBound && fabsf(x.h.y) < pow2f(46) &&
+          fabsf(x.l.y) < kLowBound;
     const float2 t = add2(x.h, bc2(kSplit24));
     const float2 rem = sub2(x.h, sub2(t, bc2(kSplit24)));  // exact, |rem| <= 2^23
-    oa = ulp_assemble(wa, t.x, __float2int_rn(rem.x) + __float2int_rn(x.l.x));
-    ob = ulp_assemble(wb, t.y, __float2int_rn(rem.y) + __float2int_rn(x.l.y));
+    const float2 lo = add2(rem, x.l);                        // see ulp_round
+    oa = ulp_assemble(wa, t.x, __float2int_rn(lo.x));
+    ob = ulp_assemble(wb, t.y, __float2int_rn(lo.y));
 }
 
 // The pair of opposite links that starts at link I (I < opp(I)).

@@ -168,6 +168,16 @@ struct StepArgs {
     const int32_t* tile_stride; // compact layout: values per link of each tile
     const ulonglong2* tinfo;    // per tile, one 16-byte record: {first fluid-mask word, tile_off << 24 | tile_stride}
     const NRec* ntab;           // [n_tiles][3^d] neighbour records (one-word tiles, float-float step) or NULL
+    // L2 prefetch of the source values ahead of the blocks that read them:
+    // block b asks the L2 for the range of work block b + pf_ahead (0: off).
+    // A copy holds pf_node_bytes per fluid node with the tiles in work-list
+    // order, so the ranges [node_begin, node_begin + count) * pf_node_bytes
+    // of the work blocks partition it, each about its own tiles' values;
+    // clamped to pf_limit bytes
+    int pf_ahead;
+    int pf_tables;  // also the block's node-list entries and neighbour records
+    int pf_node_bytes;
+    long long pf_limit;
     int n_tiles;
     long long n_nodes;          // fluid nodes (entries of the work list)
     const int32_t* gtab;        // FP64 gather table [q + 1][gtab_pitch] (see k_gather_table) or NULL

@@ -23,8 +23,15 @@ __global__ void __launch_bounds__(BT, (!PERSIST && BT <= 256) ? 1536 / BT : 1) k
     __shared__ NeighShared<TL, work_tiles()> sh;
     // one work block per thread block, or (persistent) a grid-stride loop over them
     for (int wbi = blockIdx.x; wbi < a.n_work_blocks; wbi += PERSIST ? (int)gridDim.x : a.n_work_blocks) {
+        // the work block that runs pf_ahead blocks later: its source range is
+        // requested from the L2 once this block's staging is done
+        const bool pf = !PERSIST && threadIdx.x == 0 && a.pf_ahead > 0 && wbi + a.pf_ahead < a.n_work_blocks;
+        WorkBlock pw{};
+        if (pf) pw = a.blocks[wbi + a.pf_ahead];
         WorkNode wn;
-        if (stage_work_at<TL, work_tiles(), BT>(sh, a, wbi, wn)) {
+        const bool active = stage_work_at<TL, work_tiles(), BT>(sh, a, wbi, wn);
+        if (pf) prefetch_work_block<TL::NN>(a, pw);
+        if (active) {
             const NodePos<A> p = node_pos<TL>(wn.node);
             T raw[L::Q];
             const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, raw);

@@ -31,8 +31,16 @@ __global__ void __launch_bounds__(BT, MINB) k_step_ff(const StepArgs a) {
     if constexpr (TL::W == 1) {
         // the neighbourhood from the per-tile neighbour records
         __shared__ RecShared<TL, work_tiles()> sh;
+        // the work block that runs pf_ahead blocks later: its source range is
+        // requested from the L2 once this block's staging is done
+        const int pfb = (int)blockIdx.x + a.pf_ahead;
+        const bool pf = threadIdx.x == 0 && a.pf_ahead > 0 && pfb < a.n_work_blocks;
+        WorkBlock pw{};
+        if (pf) pw = a.blocks[pfb];
         WorkNode wn;
-        if (!stage_work_rec<TL, work_tiles(), BT>(sh, a, wn)) return;
+        const bool active = stage_work_rec<TL, work_tiles(), BT>(sh, a, wn);
+        if (pf) prefetch_work_block<TL::NN>(a, pw);
+        if (!active) return;
         const NodePos<A> p = node_pos<TL>(wn.node);
         T b[L::Q];
         int stride;

@@ -351,6 +351,39 @@ __device__ __forceinline__ void cp_async8_l1(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Ask the L2 for [p, p + bytes) (16-byte aligned, a multiple of 16 bytes);
+// no registers or shared memory are held while the lines arrive.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// [b0, b1) of an array of `limit` bytes, widened to 16-byte bounds (the end
+// clamped to the last whole 16 bytes), requested from the L2.
+__device__ __forceinline__ void prefetch_l2_range(const void* base, long long b0, long long b1, long long limit) {
+    b0 &= ~15ll;
+    b1 = (b1 + 15) & ~15ll;
+    if (b1 > (limit & ~15ll)) b1 = limit & ~15ll;
+    if (b1 > b0) prefetch_l2_bulk(static_cast<const char*>(base) + b0, (unsigned)(b1 - b0));
+}
+
+// What work block `w` will read, requested from the L2 ahead of its run (see
+// StepArgs::pf_ahead): its source range and, with pf_tables, its entries of
+// the node list and its tiles' neighbour records (or neighbour indices).
+template <int NN>
+__device__ __forceinline__ void prefetch_work_block(const StepArgs& a, const WorkBlock& w) {
+    const long long nb = a.pf_node_bytes;
+    prefetch_l2_range(a.src, w.node_begin * nb, (long long)(w.node_begin + w.count) * nb, a.pf_limit);
+    if (a.pf_tables) {
+        prefetch_l2_range(a.nodes, 4ll * w.node_begin, 4ll * (w.node_begin + w.count), 4ll * a.n_nodes);
+        const long long t0 = (long long)w.tile_begin * NN, t1 = (long long)(w.tile_begin + w.n_tiles) * NN;
+        if (a.ntab)
+            prefetch_l2_range(a.ntab, t0 * (long long)sizeof(NRec), t1 * (long long)sizeof(NRec),
+                              (long long)a.n_tiles * NN * (long long)sizeof(NRec));
+        else
+            prefetch_l2_range(a.nbr, 4 * t0, 4 * t1, 4ll * a.n_tiles * NN);
+    }
+}
+
 template <class TL, int KMAX, int BT>
 __device__ __forceinline__ bool stage_work_rec(RecShared<TL, KMAX>& sh, const StepArgs& a, WorkNode& wn) {
     const WorkBlock wb = a.blocks[blockIdx.x];

@@ -45,7 +45,8 @@ class lbm_params(ctypes.Structure):
                 ("periodic", ctypes.c_int * 3), ("tau", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("storage", ctypes.c_int),
                 ("arith", ctypes.c_int), ("f16_scale", ctypes.c_double),
-                ("block_nodes", ctypes.c_int), ("persistent", ctypes.c_int), ("layout", ctypes.c_int)]
+                ("block_nodes", ctypes.c_int), ("persistent", ctypes.c_int), ("layout", ctypes.c_int),
+                ("prefetch_blocks", ctypes.c_int)]
 
 
 class lbm_tiling(ctypes.Structure):
@@ -125,7 +126,7 @@ def lbm_last_error() -> str:
 def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0, 0.0, 0.0),
                 rho0=1.0, model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64,
                 arith=LBM_ARITH_AUTO, f16_scale=0.0, block_nodes=0, persistent=0,
-                layout=LBM_LAYOUT_T2C) -> lbm_params:
+                layout=LBM_LAYOUT_T2C, prefetch_blocks=0) -> lbm_params:
     """lbm_params from a mask shape (nz, ny, nx) or (ny, nx)."""
     if len(shape) == 2:
         shape = (1,) + tuple(shape)
@@ -137,6 +138,7 @@ def make_params(lattice, shape, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0.0,
         p.force[k] = float(force[k]) if k < len(force) else 0.0
     p.tau, p.rho0, p.storage, p.arith, p.f16_scale = float(tau), float(rho0), storage, arith, float(f16_scale)
     p.block_nodes, p.persistent, p.layout = int(block_nodes), int(persistent), int(layout)
+    p.prefetch_blocks = int(prefetch_blocks)
     return p
 
 
@@ -274,13 +276,14 @@ class BatchSolver:
 
     def __init__(self, masks, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
                  model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F32S, arith=LBM_ARITH_AUTO,
-                 f16_scale=0.0, block_nodes=0, persistent=0, layout=LBM_LAYOUT_T2C, device="cuda"):
+                 f16_scale=0.0, block_nodes=0, persistent=0, layout=LBM_LAYOUT_T2C, device="cuda",
+                 prefetch_blocks=0):
         import torch
 
         self.masks = [np.ascontiguousarray(m[None] if m.ndim == 2 else m, np.uint8) for m in masks]
         self.q = lattice
         self.params = make_params(lattice, self.masks[0].shape, tile_a, periodic, tau, force, rho0, model,
-                                  storage, arith, f16_scale, block_nodes, persistent, layout)
+                                  storage, arith, f16_scale, block_nodes, persistent, layout, prefetch_blocks)
         self.tiling = lbm_build_tilemap_batch(self.params, self.masks)
         nbytes = max(int(self.tiling.pdf_bytes), 256)
         self.device = torch.device(device)
@@ -323,7 +326,7 @@ class Solver:
     def __init__(self, mask, lattice, tile_a, periodic=(0, 0, 0), tau=0.6, force=(0, 0, 0), rho0=1.0,
                  model=LBM_QUASI_COMPRESSIBLE, storage=LBM_STORE_F64, arith=LBM_ARITH_AUTO,
                  f16_scale=0.0, rho_init=None, u_init=None, block_nodes=0, persistent=0,
-                 layout=LBM_LAYOUT_T2C, device="cuda"):
+                 layout=LBM_LAYOUT_T2C, device="cuda", prefetch_blocks=0):
         import torch
 
         self.torch = torch
@@ -334,7 +337,7 @@ class Solver:
         self.shape = self.mask.shape
         self.q = lattice
         self.params = make_params(lattice, self.shape, tile_a, periodic, tau, force, rho0, model, storage,
-                                  arith, f16_scale, block_nodes, persistent, layout)
+                                  arith, f16_scale, block_nodes, persistent, layout, prefetch_blocks)
         self.tiling, _, _ = lbm_build_tilemap(self.params, self.mask, want_map=False, want_nbr=False)
         nbytes = max(int(self.tiling.pdf_bytes), 256)
         self.device = torch.device(device)

@@ -179,6 +179,27 @@ def test_work_block_size_keeps_the_bits():
         lbm.Solver(m2, 9, 16, (1, 0, 0), 0.8, (1e-6, 0, 0), arith=lbm.LBM_ARITH_FF, block_nodes=128)
 
 
+@pytest.mark.parametrize("storage", [lbm.LBM_STORE_F64, lbm.LBM_STORE_F32S], ids=["f64", "f32s"])
+def test_l2_prefetch_distance_keeps_the_bits(storage):
+    """The L2 prefetch of the work block k blocks ahead (off, the default,
+    one block ahead, further than the grid) only moves data into the L2: the
+    same bits for every distance.  It also stays within the copy and the
+    tables at the last blocks."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(48, 40, 36), seed=13, r_min=2, r_max=5, target_fluid=0.3)
+    out = []
+    for pf in (-1, 0, 1, 7, 10 ** 6):
+        s = lbm.Solver(mask, 19, 4, (1, 0, 0), 0.6, (1e-5, 0, 0), storage=storage, prefetch_blocks=pf)
+        try:
+            s.step(30)
+            out.append(s.export_pdfs())
+        finally:
+            s.close()
+    fl = mask.astype(bool)
+    for o in out[1:]:
+        assert np.array_equal(out[0][:, fl], o[:, fl])
+
+
 @pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 def test_moments_and_stats(oracle, arith):
     _cuda()
