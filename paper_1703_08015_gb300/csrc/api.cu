@@ -13,7 +13,7 @@ StepLaunch select_step_f64(int lattice, int a, int model, int storage);
 StepLaunch select_step_fixed(int lattice, int a, int model);
 StepLaunch select_step_f32(int lattice, int a, int model, int storage, int block_nodes, int persistent);
 
-StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes);
+StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes, int fax);
 
 // Fluid nodes per work block of the step kernel: the caller's choice, else
 // 128 for the float-float FP64 step on tiles of at most 128 nodes where a
@@ -37,11 +37,11 @@ StepLaunch select_step(const lbm_params* p) {
         const bool ff = arith == LBM_ARITH_FF || arith == LBM_ARITH_AUTO || arith == LBM_ARITH_FF_TABLE;
         const int bn = step_block_nodes(p);
         if (bn != work_threads_for(lattice, a))  // 128-node work blocks: float-float only
-            return ff ? select_step_ff(lattice, a, model, bn) : nullptr;
+            return ff ? select_step_ff(lattice, a, model, bn, ff_force_axis(lattice, p->force)) : nullptr;
         StepLaunch f = nullptr;
         if (arith == LBM_ARITH_F64) return select_step_f64(lattice, a, model, storage);
         if (arith == LBM_ARITH_FIXED) f = select_step_fixed(lattice, a, model);
-        if (ff) f = select_step_ff(lattice, a, model, 0);
+        if (ff) f = select_step_ff(lattice, a, model, 0, ff_force_axis(lattice, p->force));
         return f ? f : select_step_f64(lattice, a, model, storage);
     }
     return select_step_f32(lattice, a, model, storage, p->block_nodes, p->persistent);

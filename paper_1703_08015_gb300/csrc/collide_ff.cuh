@@ -24,19 +24,22 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
     return ff{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
 
-// Sums are renormalised (after cancellation the low part could otherwise
-// grow to the size of the high part, and a following product would evaluate
-// it in single precision); products return (p, e) with |e| within a few ulps
-// of p, which every consumer accepts, saving a two-sum per product.
+// x + y renormalised (the low part within half an ulp of the high part);
+// products return (p, e) with |e| within a few ulps of p, which every
+// consumer accepts, saving a two-sum per product.
 __device__ __forceinline__ ff ff_add(ff x, ff y) {
     const ff s = two_sum(x.h, y.h);
     return fast2(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
 }
 
-// x + y without the final renormalisation, for sums that only feed further
-// sums (ff_sum3): the error is the same as ff_add's, but the low part may
-// exceed half an ulp of the high part after cancellation, which a following
-// product would evaluate in single precision.
+// x + y without the final renormalisation.  The value is as accurate as
+// ff_add's, but after cancellation the low part may exceed half an ulp of the
+// high part: it stays within about 1.5 ulps of the larger operand's high
+// part.  A product then evaluates that low part in single precision, an
+// error of about 2^-47 times the operands' magnitudes, the same order as a
+// float-float product's own rounding; every sum of the collision that feeds
+// a product or a further sum is taken this way (the results are rounded to
+// FP64 in units of ulp(w), where such errors are a small fraction of a unit).
 __device__ __forceinline__ ff ff_add_lazy(ff x, ff y) {
     const ff s = two_sum(x.h, y.h);
     return ff{s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l))};
@@ -242,11 +245,6 @@ __device__ __forceinline__ ff2 two_sum_2(float2 a, float2 b) {
     return ff2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
 }
 
-__device__ __forceinline__ ff2 ff_add_2(ff2 x, ff2 y) {
-    const ff2 s = two_sum_2(x.h, y.h);
-    return fast2_2(s.h, add2(s.l, add2(x.l, y.l)));
-}
-
 __device__ __forceinline__ ff2 ff_add_lazy_2(ff2 x, ff2 y) {
     const ff2 s = two_sum_2(x.h, y.h);
     return ff2{s.h, add2(s.l, add2(x.l, y.l))};
@@ -335,22 +333,57 @@ struct FFPair {
 // The first links of the pairs of opposite links, in link order, grouped two
 // by two when both pairs have the same number of nonzero components (and so
 // the same sequence of operations); a pair left alone packs its two links.
-template <class L>
+// FAX >= 0: the body force lies along axis FAX (or is zero), so the pairs
+// with c_i . F = 0 carry no forcing terms (beta_i = so_i = 0); they are
+// grouped together (nob[g]) and skip those terms.  A group that keeps its
+// forcing terms holds the same pairs as in the general grouping (FAX = -1),
+// whose per-group constants it reads; the lone pair reads per-link ones.
+template <class L, int FAX = -1>
 struct FFGroups;
-template <>
-struct FFGroups<D2Q9> {
+template <int FAX>
+struct FFGroups<D2Q9, FAX> {
+    static_assert(FAX == -1, "D2Q9 takes the general grouping");
     static constexpr int n = 2;
     static constexpr int a[2] = {1, 5}, b[2] = {2, 6};
+    static constexpr bool nob[2] = {false, false};
     static constexpr int lone = -1;
 };
 template <>
-struct FFGroups<D3Q19> {
+struct FFGroups<D3Q19, -1> {
     static constexpr int n = 4;
     static constexpr int a[4] = {1, 7, 11, 15}, b[4] = {3, 9, 13, 17};
+    static constexpr bool nob[4] = {false, false, false, false};
+    static constexpr int lone = 5;
+};
+template <>
+struct FFGroups<D3Q19, 0> {  // F along x: (3,4)+(5,6) and (15,16)+(17,18) unforced
+    static constexpr int n = 4;
+    static constexpr int a[4] = {3, 7, 11, 15}, b[4] = {5, 9, 13, 17};
+    static constexpr bool nob[4] = {true, false, false, true};
+    static constexpr int lone = 1;
+};
+template <>
+struct FFGroups<D3Q19, 1> {  // F along y: (1,2)+(5,6) and (11,12)+(13,14) unforced
+    static constexpr int n = 4;
+    static constexpr int a[4] = {1, 7, 11, 15}, b[4] = {5, 9, 13, 17};
+    static constexpr bool nob[4] = {true, false, true, false};
+    static constexpr int lone = 3;
+};
+template <>
+struct FFGroups<D3Q19, 2> {  // F along z: (1,2)+(3,4) and (7,8)+(9,10) unforced
+    static constexpr int n = 4;
+    static constexpr int a[4] = {1, 7, 11, 15}, b[4] = {3, 9, 13, 17};
+    static constexpr bool nob[4] = {true, true, false, false};
     static constexpr int lone = 5;
 };
 
-template <class L, int MODEL>
+// Component of link I along axis X (0 for X < 0).
+template <class L, int I, int X>
+constexpr int link_comp() {
+    return X == 0 ? Link<L, I>::cx : (X == 1 ? Link<L, I>::cy : (X == 2 ? Link<L, I>::cz : 0));
+}
+
+template <class L, int MODEL, int FAX = -1>
 __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], const FixedConsts& k,
                                            const FFConsts& c, unsigned long long* out, int stride) {
     constexpr int Q = L::Q;
@@ -416,14 +449,14 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         const float er = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(rho.l, r0));
         RINV = fast2(r0, __fmul_rn(r0, er));
     }
-    // gamma = 1.5 w |p|^2 + 3 (1 - w/2) p.F, p = j + F/2
-    // (sums that feed a product are renormalised, the others are lazy)
+    // gamma = 1.5 w |p|^2 + 3 (1 - w/2) p.F, p = j + F/2 (lazy sums, see
+    // ff_add_lazy)
     ff gamma;
     {
         const ff2 sq = ff_sqr_2(JXY);
         const ff2 kfx = ff_mul_2(JXY, ff2_k(c.kf01));
-        const ff jj = ff_add(ff_add_lazy(lane0(sq), lane1(sq)), ff_sqr(JZ));
-        gamma = ff_add(ff_mul(jj, ff_c(c.g1)), ff_add_lazy(ff_add_lazy(lane0(kfx), lane1(kfx)), ff_mul(JZ, ff_c(c.kf[2]))));
+        const ff jj = ff_add_lazy(ff_add_lazy(lane0(sq), lane1(sq)), ff_sqr(JZ));
+        gamma = ff_add_lazy(ff_mul(jj, ff_c(c.g1)), ff_add_lazy(ff_add_lazy(lane0(kfx), lane1(kfx)), ff_mul(JZ, ff_c(c.kf[2]))));
     }
     // per class, in units of ulp(w_c): V = w_c / rho, C = w w_c drho - gamma V;
     // classes 1 and 2 in both lanes (each group of pairs is single-class), each
@@ -443,12 +476,16 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         CC = ff_add_lazy_2(ff_mul_2(ff2_bc(DR), ff2_k(rcc)), ff2_neg(ff_mul_2(ff2_bc(gamma), VV)));
     };
     // two pairs of opposite links at once: lanes (pair A, pair B)
+    using GR = FFGroups<L, FAX>;
     auto group = [&](auto G, const ff2& VV, const ff2& CC) {
         constexpr int g = decltype(G)::value;
-        using PA = FFPair<L, FFGroups<L>::a[g]>;
-        using PB = FFPair<L, FFGroups<L>::b[g]>;
+        using PA = FFPair<L, GR::a[g]>;
+        using PB = FFPair<L, GR::b[g]>;
         static_assert(PA::n_comp == PB::n_comp, "grouped pairs take the same operations");
         static_assert(PA::cls == PB::cls && PA::cls > 0, "a group takes one class of links");
+        static_assert(GR::nob[g] ? (link_comp<L, GR::a[g], FAX>() == 0 && link_comp<L, GR::b[g], FAX>() == 0)
+                                 : (GR::a[g] == FFGroups<L>::a[g] && GR::b[g] == FFGroups<L>::b[g]),
+                      "an unforced group has c.F = 0; a forced one reads the general group's constants");
         // y = c_i . p
         auto comp = [&](auto Kc) {
             constexpr int kk = decltype(Kc)::value;
@@ -456,10 +493,19 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
             return pack2(PA::sign(kk) > 0 ? a : ff_neg(a), PB::sign(kk) > 0 ? bb : ff_neg(bb));
         };
         ff2 Y = comp(std::integral_constant<int, 0>{});
-        static_for<1, PA::n_comp>([&](auto Kc) { Y = ff_add_2(Y, comp(Kc)); });
-        const ff2 T = ff_mul_2(Y, ff_add_2(ff_mul_2(Y, ALPHA), ff2_k(c.beta2[g])));
+        static_for<1, PA::n_comp>([&](auto Kc) { Y = ff_add_lazy_2(Y, comp(Kc)); });
+        // without forcing terms the sums with beta = so = 0 are left out: adding
+        // a zero float-float lazily returns its operand, so the bits are the
+        // general grouping's
+        ff2 T, O;
+        if constexpr (GR::nob[g]) {
+            T = ff_mul_2(Y, ff_mul_2(Y, ALPHA));
+            O = ff_mul_2(Y, ff2_k(c.j2[g]));
+        } else {
+            T = ff_mul_2(Y, ff_add_lazy_2(ff_mul_2(Y, ALPHA), ff2_k(c.beta2[g])));
+            O = ff_add_lazy_2(ff_mul_2(Y, ff2_k(c.j2[g])), ff2_k(c.so2[g]));
+        }
         const ff2 E = ff_add_lazy_2(CC, ff_mul_2(T, VV));
-        const ff2 O = ff_add_lazy_2(ff_mul_2(Y, ff2_k(c.j2[g])), ff2_k(c.so2[g]));
         const ff2 xi = ff_sum3_2(ff_mul_2(d_to_ff_2(d[PA::i], d[PB::i]), KEEP), E, O);
         unsigned long long r0, r1;
         ulp_round_2(xi, (unsigned long long)k.w_bits[PA::cls], (unsigned long long)k.w_bits[PB::cls], ok, r0, r1);
@@ -477,9 +523,9 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         static_for<0, P::n_comp>([&](auto Kc) {
             constexpr int kk = decltype(Kc)::value;
             const ff t = P::sign(kk) > 0 ? J[P::axis(kk)] : ff_neg(J[P::axis(kk)]);
-            Y = kk == 0 ? t : ff_add(Y, t);
+            Y = kk == 0 ? t : ff_add_lazy(Y, t);
         });
-        const ff T = ff_mul(Y, ff_add(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[P::i])));
+        const ff T = ff_mul(Y, ff_add_lazy(ff_mul(Y, ff_c(c.alpha)), ff_c(c.beta[P::i])));
         const ff E = ff_add_lazy(lane0(CC), ff_mul(T, lane0(VV)));
         const ff O = ff_add_lazy(ff_mul(Y, ff_c(c.j[P::cls])), ff_c(c.so[P::i]));
         const ff2 x = ff_sum3_2(ff_mul_2(d_to_ff_2(d[P::i], d[P::j]), KEEP), ff2_bc(E), pack2(O, ff_neg(O)));
@@ -488,18 +534,20 @@ __device__ __forceinline__ bool collide_ff(const unsigned long long (&b)[L::Q], 
         out[P::i * stride] = r0;
         out[P::j * stride] = r1;
     };
-    static_assert(FFGroups<L>::lone < 0 || Link<L, (FFGroups<L>::lone > 0 ? FFGroups<L>::lone : 1)>::cls == 1,
-                  "the lone pair is of class 1");
+    static_assert(GR::lone < 0 || Link<L, (GR::lone > 0 ? GR::lone : 1)>::cls == 1, "the lone pair is of class 1");
     {  // class 1: the first group and the lone pair
         ff2 VV, CC;
         class_consts(c.w11, c.rho11, VV, CC);
+        // (the order only moves register pressure: with a force axis the lone
+        // pair first spilled less and measured 2 % faster, in general last)
+        if constexpr (FAX >= 0 && GR::lone > 0) lone(std::integral_constant<int, GR::lone>{}, VV, CC);
         group(std::integral_constant<int, 0>{}, VV, CC);
-        if constexpr (FFGroups<L>::lone > 0) lone(std::integral_constant<int, FFGroups<L>::lone>{}, VV, CC);
+        if constexpr (FAX < 0 && GR::lone > 0) lone(std::integral_constant<int, GR::lone>{}, VV, CC);
     }
     {  // class 2: the other groups
         ff2 VV, CC;
         class_consts(c.w22, c.rho22, VV, CC);
-        static_for<1, FFGroups<L>::n>([&](auto G) { group(G, VV, CC); });
+        static_for<1, GR::n>([&](auto G) { group(G, VV, CC); });
     }
     return ok;
 }

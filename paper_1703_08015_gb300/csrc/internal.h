@@ -236,6 +236,10 @@ StepLaunch select_step_tgb(const lbm_params* p);
 // The float-float FP64 step that reads its sources from a gather table, and
 // the kernel that builds the table once (nullptr when not compiled).
 StepLaunch select_step_ff_table(int lattice, int a, int model);
+// The axis of a D3Q19 body force with one nonzero component (0 for no force),
+// else -1: the float-float step then leaves out the forcing terms of the
+// links with c_i . F = 0.
+int ff_force_axis(int lattice, const double force[3]);
 StepLaunch select_gather_table_builder(int lattice, int a);
 StepLaunch select_tgb_publish(int lattice, int a, int storage);
 long long tgb_ghost_per_tile(int lattice, int a);

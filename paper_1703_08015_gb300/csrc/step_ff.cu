@@ -19,12 +19,13 @@
 // ~w_i/64, |j| >= 1/16, |rho - 1| >= 1/32, NaN, negative values) are
 // recomputed in native FP64.
 #include <cmath>
+#include <type_traits>
 
 #include "collide_ff.cuh"
 
 namespace lbm {
 
-template <class L, int A, int MODEL, int MINB, int BT>
+template <class L, int A, int MODEL, int MINB, int BT, int FAX>
 __global__ void __launch_bounds__(BT, MINB) k_step_ff(const StepArgs a) {
     using TL = Tile<L, A>;
     using T = unsigned long long;
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(BT, MINB) k_step_ff(const StepArgs a) {
         T* out = gather_rec<L, A, work_tiles(), T>(sh, a.src, a.dst, wn.lt, wn.node, p, b, stride);
         // out of range: the same update in native FP64 (a call, so that its
         // registers do not weigh on the float-float path)
-        if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) update_fp64_rec<L, A, MODEL, work_tiles()>(sh, a, wn, p);
+        if (!collide_ff<L, MODEL, FAX>(b, a.fx, a.ffc, out, stride))
+            update_fp64_rec<L, A, MODEL, work_tiles()>(sh, a, wn, p);
     } else {
         __shared__ NeighShared<TL, work_tiles()> sh;
         WorkNode wn;
@@ -57,14 +59,15 @@ __global__ void __launch_bounds__(BT, MINB) k_step_ff(const StepArgs a) {
         const int rank = gather<L, A, work_tiles(), T>(sh, a.src, wn.lt, wn.node, p, b);
         const int stride = sh.loc[wn.lt][TL::CENTER].y;
         T* out = own_slot<TL, work_tiles(), T>(sh, a.dst, wn.lt, rank);
-        if (!collide_ff<L, MODEL>(b, a.fx, a.ffc, out, stride)) update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
+        if (!collide_ff<L, MODEL, FAX>(b, a.fx, a.ffc, out, stride))
+            update_fp64<L, A, MODEL, work_tiles()>(sh, a, wn, p, out, stride);
     }
 }
 
-template <class L, int A, int MODEL, int MINB, int BT>
+template <class L, int A, int MODEL, int MINB, int BT, int FAX>
 cudaError_t launch_step_ff(const StepArgs& a, cudaStream_t s) {
     if (a.n_work_blocks == 0) return cudaSuccess;
-    k_step_ff<L, A, MODEL, MINB, BT><<<a.n_work_blocks, BT, 0, s>>>(a);
+    k_step_ff<L, A, MODEL, MINB, BT, FAX><<<a.n_work_blocks, BT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -132,34 +135,59 @@ void ff_consts(const lbm_params* p, FFConsts* k) {
 // to 72 registers, 44 B of spill): 28 resident warps hide more of the gather
 // latency than 24 at 80 registers (328 against 348 us per 256^3 step; 64
 // registers and eight blocks spill 100 B, 345 us).
-template <class L, int A, int BT>
-static StepLaunch pick_bt(int model) {
+template <class L, int A, int BT, int FAX>
+static StepLaunch pick_model(int model) {
     constexpr int MINB = BT == work_threads<L, A>() ? fp64_step_min_blocks<L, A>() : 7;
-    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_ff<L, A, LBM_QUASI_COMPRESSIBLE, MINB, BT>
-                                           : &launch_step_ff<L, A, LBM_INCOMPRESSIBLE, MINB, BT>;
+    return model == LBM_QUASI_COMPRESSIBLE ? &launch_step_ff<L, A, LBM_QUASI_COMPRESSIBLE, MINB, BT, FAX>
+                                           : &launch_step_ff<L, A, LBM_INCOMPRESSIBLE, MINB, BT, FAX>;
+}
+
+// The default D3Q19 step (4^3 tiles, 128-node blocks) also comes with the
+// groupings for a body force along one axis (FFGroups), which leave out the
+// forcing terms of the four pairs with c_i . F = 0: the same bits in fewer
+// instructions.
+template <class L, int A, int BT>
+static StepLaunch pick_bt(int model, int fax) {
+    if constexpr (std::is_same<L, D3Q19>::value && A == 4 && BT == 128) {
+        if (fax == 0) return pick_model<L, A, BT, 0>(model);
+        if (fax == 1) return pick_model<L, A, BT, 1>(model);
+        if (fax == 2) return pick_model<L, A, BT, 2>(model);
+    }
+    return pick_model<L, A, BT, -1>(model);
 }
 
 // block_nodes: 0 (the default work blocks) or 128 where they hold 256 nodes
 // and a tile fits in 128 (a work block never splits a tile)
 template <class L, int A>
-static StepLaunch pick(int model, int block_nodes) {
+static StepLaunch pick(int model, int block_nodes, int fax) {
     constexpr int BD = work_threads<L, A>();
     if constexpr (BD == 256 && Tile<L, A>::NT <= 128) {
-        if (block_nodes == 128) return pick_bt<L, A, 128>(model);
+        if (block_nodes == 128) return pick_bt<L, A, 128>(model, fax);
     }
 
     if (block_nodes != 0 && block_nodes != BD) return nullptr;
-    return pick_bt<L, A, BD>(model);
+    return pick_bt<L, A, BD>(model, fax);
 }
 
-StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes) {
+int ff_force_axis(int lattice, const double force[3]) {
+    if (lattice != LBM_D3Q19) return -1;
+    int nz = 0, ax = 0;
+    for (int k = 0; k < 3; k++)
+        if (force[k] != 0.0) {
+            nz++;
+            ax = k;
+        }
+    return nz <= 1 ? ax : -1;
+}
+
+StepLaunch select_step_ff(int lattice, int a, int model, int block_nodes, int fax) {
     if (lattice == LBM_D2Q9) {
-        if (a == 8) return pick<D2Q9, 8>(model, block_nodes);
-        if (a == 16) return pick<D2Q9, 16>(model, block_nodes);
-        if (a == 32) return pick<D2Q9, 32>(model, block_nodes);
+        if (a == 8) return pick<D2Q9, 8>(model, block_nodes, -1);
+        if (a == 16) return pick<D2Q9, 16>(model, block_nodes, -1);
+        if (a == 32) return pick<D2Q9, 32>(model, block_nodes, -1);
     } else if (lattice == LBM_D3Q19) {
-        if (a == 4) return pick<D3Q19, 4>(model, block_nodes);
-        if (a == 8) return pick<D3Q19, 8>(model, block_nodes);
+        if (a == 4) return pick<D3Q19, 4>(model, block_nodes, fax);
+        if (a == 8) return pick<D3Q19, 8>(model, block_nodes, fax);
     }
     return nullptr;
 }

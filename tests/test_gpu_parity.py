@@ -200,6 +200,31 @@ def test_l2_prefetch_distance_keeps_the_bits(storage):
         assert np.array_equal(out[0][:, fl], o[:, fl])
 
 
+@pytest.mark.parametrize("model", [0, 1], ids=["quasi", "incompressible"])
+@pytest.mark.parametrize("force", [(1e-5, 0, 0), (0, -2e-5, 0), (0, 0, 1e-5), (0, 0, 0)],
+                         ids=["fx", "fy", "fz", "nof"])
+def test_force_axis_groupings_keep_the_bits(oracle, force, model):
+    """With the body force along one axis (or none) the default D3Q19 step
+    leaves out the forcing terms of the links with c_i . F = 0: the same bits
+    as the general float-float update (here the ghost-buffer layout's), and
+    the oracle within 1e-12."""
+    _cuda()
+    mask, _ = geo.sphere_pack_3d(shape=(28, 24, 20), seed=17, r_min=2, r_max=4, target_fluid=0.4)
+    per, tau, steps = (1, 1, 1), 0.62, 60
+    out = {}
+    for layout in (lbm.LBM_LAYOUT_T2C, lbm.LBM_LAYOUT_TGB):
+        s = lbm.Solver(mask, 19, 4, per, tau, force, model=model, layout=layout)
+        try:
+            s.step(steps)
+            out[layout] = s.export_pdfs()
+        finally:
+            s.close()
+    fl = mask.astype(bool)
+    assert np.array_equal(out[lbm.LBM_LAYOUT_T2C][:, fl], out[lbm.LBM_LAYOUT_TGB][:, fl])
+    ref = oracle.run(19, mask, per, tau, force, oracle.init(19, mask, model=model), steps, model=model)
+    assert max_rel(out[lbm.LBM_LAYOUT_T2C], ref, mask) <= TOL
+
+
 @pytest.mark.parametrize("arith", ARITHS, ids=ARITH_IDS)
 def test_moments_and_stats(oracle, arith):
     _cuda()
