@@ -122,12 +122,14 @@ typedef struct lbm_params {
                          blocks as fit on the GPU at once loop over the work list */
     int layout;       /* LBM_LAYOUT_T2C (two PDF copies, default) or LBM_LAYOUT_TGB
                          (one copy updated in place plus ghost buffers, Sec. 3.1) */
-    int prefetch_blocks; /* LBM_LAYOUT_T2C (not in the paper): each block of the step
-                         kernel asks the L2 for the source values of the work block
-                         this many blocks ahead, so that its gathers find them there
-                         (the FP32 storage forms also for that block's node list and
-                         neighbour indices); 0 = default (4 per SM), < 0 = off.
-                         Timing only: results do not depend on it */
+    int prefetch_blocks; /* not in the paper: in the float-float FP64 step on tiles of
+                         one mask word (4^3, 8^2) and the FP32 storage forms' step
+                         (LBM_LAYOUT_T2C, not persistent), each block asks the L2 for
+                         the source values of the work block this many blocks ahead,
+                         so that its gathers find them there (the FP32 forms also for
+                         that block's node list and neighbour indices); 0 = default
+                         (4 per SM), < 0 = off.  Timing only: results do not depend
+                         on it */
 } lbm_params;
 
 typedef struct lbm_tiling {
@@ -271,15 +273,14 @@ int lbm_import_pdfs(lbm_ctx* ctx, const double* pdfs, int64_t step, int flags,
  * tiles of 4^3 or 8^2 nodes, or 8 tiles of 8^3, 16^2 or 32^2 nodes, so
  * tilings that need more than LBM_NOALLOC_MAX_BLOCKS blocks (more than
  * 262,144 non-empty 4^3 tiles, for example) are rejected with
- * LBM_ERR_CAPACITY.  The
- * device that was current at lbm_init must be current (else LBM_ERR_ARG).
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  A
- * cudaDeviceReset invalidates that address: calls after one are not
- * supported.  All
- * calls share the one array, which keeps the last call's contents: every
- * block writes its slots before they are read, so nothing has to start at
- * zero, but calls whose kernels overlap on the GPU race with each other.
+ * LBM_ERR_CAPACITY.  The device that was current at lbm_init must be current
+ * (else LBM_ERR_ARG).  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  A cudaDeviceReset invalidates that address: calls after
+ * one are not supported.  All calls share the one array, which keeps the
+ * last call's contents: every block writes its slots before they are read,
+ * so nothing has to start at zero, but calls whose kernels overlap on the
+ * GPU race with each other.
  * Calls no cudaMalloc, cudaFree or allocating library routine.
  * Errors: LBM_ERR_ARG, LBM_ERR_CAPACITY, LBM_ERR_CUDA. */
 int lbm_stats_noalloc(const lbm_ctx* ctx, double* stats_dev, void* stream);
