@@ -735,7 +735,8 @@ def run_batch(args):
     best, trials = autotune.tune(masks, 19, storage, per, tau, force)
     t_tune = time.perf_counter() - t0
     b = lbm.BatchSolver(masks, 19, best["tile_a"], per, tau, force, storage=storage,
-                        block_nodes=best["block_nodes"], persistent=best["persistent"], device=dev)
+                        block_nodes=best["block_nodes"], persistent=best["persistent"],
+                        prefetch_blocks=best.get("prefetch_blocks", 0), device=dev)
     n_fluid = int(b.tiling.n_fluid)
     b.step(max(3, args.warmup))
     b.stats(residual=True)

@@ -2,9 +2,10 @@
 
 For a set of geometries (a batch or a single one) it times every candidate
 mapping -- tile edge a, fluid nodes per step-kernel block, persistent or
-one-block-per-work-block grid -- for a few steps with CUDA events on the
-launching stream, keeps the fastest, and caches the choice per GPU, lattice,
-storage and workload signature in ``_build/autotune.json``.  Every candidate
+one-block-per-work-block grid, and for the latter the L2 prefetch of the
+work block four per SM ahead on or off -- for a few steps with CUDA events on
+the launching stream, keeps the fastest, and caches the choice per GPU,
+lattice, storage and workload signature in ``_build/autotune.json``.  Every candidate
 computes the same update (the tests check bit equality across mappings), so
 tuning only changes speed.
 """
@@ -39,8 +40,15 @@ def candidates(lattice, storage, masks, periodic):
         pers = [0, 1] if storage != lbm.LBM_STORE_F64 else [0]
         for bn in blocks:
             for pe in pers:
-                out.append({"tile_a": a, "block_nodes": bn, "persistent": pe})
+                # the persistent grid takes no prefetch; copies that fit the
+                # L2 can run faster without it
+                for pf in ([0, -1] if not pe else [0]):
+                    out.append({"tile_a": a, "block_nodes": bn, "persistent": pe, "prefetch_blocks": pf})
     return out
+
+
+def mapping_name(cfg):
+    return f"a{cfg['tile_a']}_b{cfg['block_nodes']}_p{cfg['persistent']}_f{cfg.get('prefetch_blocks', 0)}"
 
 
 def _signature(lattice, storage, masks):
@@ -56,7 +64,8 @@ def time_mapping(masks, lattice, cfg, storage, periodic, tau, force, steps=40, d
     import torch
 
     b = lbm.BatchSolver(masks, lattice, cfg["tile_a"], periodic, tau, force, storage=storage,
-                        block_nodes=cfg["block_nodes"], persistent=cfg["persistent"], device=device)
+                        block_nodes=cfg["block_nodes"], persistent=cfg["persistent"],
+                        prefetch_blocks=cfg.get("prefetch_blocks", 0), device=device)
     try:
         b.step(16)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -83,15 +92,14 @@ def tune(masks, lattice, storage=lbm.LBM_STORE_F32S, periodic=(1, 0, 0), tau=0.6
     if use_cache and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
-        if key in cache:
+        if key in cache and "prefetch_blocks" in cache[key]["best"]:
             return cache[key]["best"], cache[key]["trials"]
-    trials = {}
+    trials, by_name = {}, {}
     for cfg in candidates(lattice, storage, masks, periodic):
-        name = f"a{cfg['tile_a']}_b{cfg['block_nodes']}_p{cfg['persistent']}"
+        name = mapping_name(cfg)
+        by_name[name] = cfg
         trials[name] = time_mapping(masks, lattice, cfg, storage, periodic, tau, force, steps, device)
-    best_name = max(trials, key=trials.get)
-    a, bn, pe = best_name[1:].split("_")
-    best = {"tile_a": int(a), "block_nodes": int(bn[1:]), "persistent": int(pe[1:])}
+    best = by_name[max(trials, key=trials.get)]
     cache[key] = {"best": best, "trials": trials, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
     with open(cache_path, "w") as f:

@@ -107,11 +107,12 @@ def test_autotune_picks_a_compiled_mapping_and_reuses_its_cache(tmp_path, monkey
     storage = lbm.LBM_STORE_F32S
     cache = tmp_path / "autotune.json"
     cands = autotune.candidates(19, storage, masks, ARGS["periodic"])
-    assert {"tile_a": 4, "block_nodes": 0, "persistent": 0} in cands
+    assert {"tile_a": 4, "block_nodes": 0, "persistent": 0, "prefetch_blocks": 0} in cands
+    assert {"tile_a": 4, "block_nodes": 0, "persistent": 0, "prefetch_blocks": -1} in cands
     best, trials = autotune.tune(masks, 19, storage, steps=8, cache_path=str(cache), **ARGS)
     assert best in cands
     assert len(trials) == len(cands) and all(v > 0 for v in trials.values())
-    assert trials[f"a{best['tile_a']}_b{best['block_nodes']}_p{best['persistent']}"] == max(trials.values())
+    assert trials[autotune.mapping_name(best)] == max(trials.values())
     assert cache.exists()
 
     def no_timing(*a, **k):
@@ -124,7 +125,7 @@ def test_autotune_picks_a_compiled_mapping_and_reuses_its_cache(tmp_path, monkey
     res = []
     for cfg in ({"tile_a": 4, "block_nodes": 0, "persistent": 0}, best):
         b = lbm.BatchSolver(masks, 19, cfg["tile_a"], storage=storage, block_nodes=cfg["block_nodes"],
-                            persistent=cfg["persistent"], **ARGS)
+                            persistent=cfg["persistent"], prefetch_blocks=cfg.get("prefetch_blocks", 0), **ARGS)
         try:
             b.step(40)
             res.append([b.export_pdfs(k) for k in range(len(masks))])
