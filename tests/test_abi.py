@@ -187,3 +187,38 @@ def test_conv_tune_validates_its_arguments():
             assert f(bz, nt) == -1, (bz, nt)
     finally:
         assert f(0, 0) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    that a C compiler gives the structures of include/lbm.h (a field added to
+    one side only would shift every later field the library reads)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    checks = {
+        "lbm_params": (lbm.lbm_params, ["lattice", "nx", "tile_a", "periodic", "tau", "force", "rho0", "storage",
+                                        "arith", "f16_scale", "block_nodes", "persistent", "layout",
+                                        "prefetch_blocks"]),
+        "lbm_tiling": (lbm.lbm_tiling, ["ntx", "n_ftiles", "n_fluid", "pdf_bytes", "ghost_bytes"]),
+        "lbm_stats": (lbm.lbm_stats, ["mass", "momentum", "u2", "du2", "residual", "n_fluid", "step"]),
+    }
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm.h"', "int main(void) {"]
+    for st, (_, fields) in checks.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st, (cls, fields) in checks.items():
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
