@@ -132,7 +132,7 @@ void ff_consts(const lbm_params* p, FFConsts* k) {
 }
 
 // Work blocks of 128 nodes run seven blocks per SM (the compiler holds them
-// to 72 registers, 44 B of spill): 28 resident warps hide more of the gather
+// to 72 registers, 40-56 B of spill): 28 resident warps hide more of the gather
 // latency than 24 at 80 registers (328 against 348 us per 256^3 step; 64
 // registers and eight blocks spill 100 B, 345 us).
 template <class L, int A, int BT, int FAX>
